@@ -48,7 +48,8 @@
  *     r = u - i0 and W = cut * q (all FP64, one rounding per operation, no
  *     fused multiply-add), bin i is inside iff |(i - i0) - r| <= W; cut <= 0
  *     means no cut (the whole grid).  Mathematically this is
- *     |nu_i - nu0| <= cut; the FP64 form fixes the decision at ties.
+ *     |nu_i - nu0| <= cut; the FP64 form fixes the decision at ties;
+ *   - a line with nu0 <= 0 has no Doppler width (Eq. gammaD) and adds nothing.
  */
 #include <complex.h>
 #include <math.h>
@@ -252,6 +253,11 @@ static int in_cut(int64_t k, double r, double W)
 static void line_range(double nu0, double nu_min, double dnu, int64_t nbins, double cut,
                        int64_t *lo, int64_t *hi)
 {
+    if (!(nu0 > 0.0)) { /* no Doppler width (Eq. gammaD is proportional to nu0): ignored */
+        *lo = 1;
+        *hi = 0;
+        return;
+    }
     if (cut <= 0.0) {
         *lo = 0;
         *hi = nbins - 1;

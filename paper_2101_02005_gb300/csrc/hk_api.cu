@@ -1,0 +1,714 @@
+// hk_api.cu -- the C ABI of libhk (declared in include/hk.h): argument
+// checks, scalar preparation in FP64, the scratch pool, the optional sort of
+// unsorted line lists, and the small per-line kernels.
+#include <cuda_runtime.h>
+
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "hk_internal.cuh"
+#include "hk_launch.h"
+
+namespace hk {
+
+static thread_local int g_last_cuda = 0;
+
+int fail_cuda(cudaError_t e)
+{
+    g_last_cuda = (int)e;
+    (void)cudaGetLastError();  // clear a non-sticky launch error
+    return HK_ECUDA;
+}
+
+// ---- scratch pool: one grow-only device buffer per device -----------------
+struct Pool {
+    char *ptr = nullptr;
+    size_t cap = 0;
+};
+static std::mutex g_pool_mu;
+static std::map<int, Pool> g_pools;
+
+static size_t pool_limit()
+{
+    const char *s = getenv("HK_POOL_LIMIT_MB");
+    double mb = s ? atof(s) : 16384.0;
+    if (!(mb > 0)) mb = 16384.0;
+    return (size_t)(mb * 1048576.0);
+}
+
+// Returns HK_OK and a buffer of at least `bytes`, or HK_ENOMEM.
+static int pool_get(size_t bytes, char **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return fail_cuda(e);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    Pool &p = g_pools[dev];
+    if (bytes > p.cap) {
+        if (bytes > pool_limit()) return HK_ENOMEM;
+        if (p.ptr) {
+            // cudaFree waits for work in flight on the device that may still use it
+            cudaFree(p.ptr);
+            p.ptr = nullptr;
+            p.cap = 0;
+        }
+        size_t want = std::max(bytes, (size_t)64 << 20);
+        want = std::min(std::max(want, bytes + bytes / 4), std::max(pool_limit(), bytes));
+        if (cudaMalloc(&p.ptr, want) != cudaSuccess) {
+            (void)cudaGetLastError();
+            if (cudaMalloc(&p.ptr, bytes) != cudaSuccess) {
+                (void)cudaGetLastError();
+                p.ptr = nullptr;
+                return HK_ENOMEM;
+            }
+            want = bytes;
+        }
+        p.cap = want;
+    }
+    *out = p.ptr;
+    return HK_OK;
+}
+
+// ---- per-device status word ---------------------------------------------------
+static std::mutex g_status_mu;
+static std::map<int, unsigned *> g_status;
+
+unsigned *status_word()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    auto it = g_status.find(dev);
+    if (it != g_status.end()) return it->second;
+    unsigned *p = nullptr;
+    if (cudaMalloc(&p, sizeof(unsigned)) != cudaSuccess || cudaMemset(p, 0, sizeof(unsigned)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    g_status[dev] = p;
+    return p;
+}
+
+static int num_sms()
+{
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        (void)cudaGetLastError();
+        n = 148;
+    }
+    cache[dev] = n;
+    return n;
+}
+
+// ---- tuning cache (hk_autotune) --------------------------------------------
+struct Tune {
+    int bpt = 4;
+    int lmax = 16384;
+};
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, Tune> g_tune;  // (device, precision) -> tuning
+
+static Tune get_tune(int precision)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find({dev, precision});
+    if (it != g_tune.end()) return it->second;
+    Tune t;
+    if (precision == HK_FP64) t.bpt = 2;
+    return t;
+}
+
+// ---- validation ------------------------------------------------------------
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
+
+static int check_lines(const hk_lines *L, bool need_fields)
+{
+    if (!L || L->n < 0) return HK_EINVAL;
+    if (L->n == 0) return HK_OK;
+    if (!L->nu0 || !finite_pos(L->mass_amu)) return HK_EINVAL;
+    if (L->s_mode != HK_S_REF && L->s_mode != HK_S_EINSTEIN_A) return HK_EINVAL;
+    if (!need_fields) return HK_OK;
+    if (!L->E_low || !L->gamma_ref || !L->n_T) return HK_EINVAL;
+    if (L->s_mode == HK_S_REF && !L->S_ref) return HK_EINVAL;
+    if (L->s_mode == HK_S_EINSTEIN_A && (!L->A || !L->g_up)) return HK_EINVAL;
+    return HK_OK;
+}
+
+static int check_grid(const hk_grid *g)
+{
+    if (!g || g->nbins <= 0 || g->nbins > 2000000000LL || !finite_pos(g->dnu) ||
+        !std::isfinite(g->nu_min))
+        return HK_EINVAL;
+    return HK_OK;
+}
+
+static int check_state(const hk_state *s)
+{
+    if (!s || !finite_pos(s->T) || !std::isfinite(s->P) || s->P < 0 || !finite_pos(s->Q_T) ||
+        !std::isfinite(s->dlnQ_dT))
+        return HK_EINVAL;
+    return HK_OK;
+}
+
+static int check_opts(const hk_opts *o)
+{
+    if (!o || !finite_pos(o->T_ref) || !finite_pos(o->P_ref) || !finite_pos(o->Q_Tref) ||
+        !std::isfinite(o->cut))
+        return HK_EINVAL;
+    if (o->cut_mode != HK_CUT_FIXED && o->cut_mode != HK_CUT_NONE) return HK_EINVAL;
+    if (o->precision != HK_FP32C && o->precision != HK_FP64) return HK_EINVAL;
+    if (o->flags & ~(HK_PER_GRAM | HK_SIGMA_F64)) return HK_EINVAL;
+    return HK_OK;
+}
+
+static GridD make_grid(const hk_grid *g, const hk_opts *o)
+{
+    GridD d;
+    d.nu_min = g->nu_min;
+    d.dnu = g->dnu;
+    d.inv_dnu = 1.0 / g->dnu;
+    d.nbins = g->nbins;
+    bool nocut = (o && o->cut_mode == HK_CUT_NONE) || !o;
+    d.cut = nocut ? 0.0 : o->cut;
+    d.W = (d.cut > 0.0) ? d.cut * d.inv_dnu : 0.0;
+    if (d.cut <= 0.0) d.cut = 0.0;
+    return d;
+}
+
+static GridD make_grid_cut(const hk_grid *g, double cut)
+{
+    GridD d;
+    d.nu_min = g->nu_min;
+    d.dnu = g->dnu;
+    d.inv_dnu = 1.0 / g->dnu;
+    d.nbins = g->nbins;
+    d.cut = cut > 0.0 ? cut : 0.0;
+    d.W = cut > 0.0 ? cut * d.inv_dnu : 0.0;
+    return d;
+}
+
+// FP64 scalars of one (species, T, P) problem.
+static Prob make_prob(const hk_lines *L, const hk_state *s, const hk_opts *o)
+{
+    Prob p;
+    memset(&p, 0, sizeof(p));
+    p.nu0 = L->nu0;
+    p.S_ref = L->S_ref;
+    p.A = L->A;
+    p.g_up = L->g_up;
+    p.E_low = L->E_low;
+    p.gamma = L->gamma_ref;
+    p.n_T = L->n_T;
+    p.n = L->n;
+    p.s_mode = L->s_mode;
+    p.pre = 0;
+    const double T = s->T;
+    if (L->s_mode == HK_S_REF) {
+        p.K2 = -kC2 * (1.0 / T - 1.0 / o->T_ref) * kInvLn2;
+        p.qratio = o->Q_Tref / s->Q_T;
+    } else {
+        p.K2 = -kC2 / T * kInvLn2;
+        p.qratio = 1.0 / (8.0 * kPI * kC * s->Q_T);
+    }
+    p.c2T = kC2 / T;
+    p.c2Tref = kC2 / o->T_ref;
+    const double m_g = L->mass_amu * kAMU;
+    p.mass_scale = (o->flags & HK_PER_GRAM) ? 1.0 / m_g : 1.0;
+    p.aD_coef = kC * std::sqrt(m_g / (2.0 * kKB * T));
+    p.log2_tratio = std::log2(o->T_ref / T);
+    p.press = s->P / o->P_ref;
+    p.inv_Pref = 1.0 / o->P_ref;
+    p.nat_coef = 1.0 / (4.0 * kPI * kC);
+    return p;
+}
+
+// ---- small per-line kernels -------------------------------------------------
+__global__ void k_strength(Prob p, double *S_out)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < p.n;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        double S, aDinv, y;
+        line_strength_f64(p, l, &S, &aDinv, &y);
+        S_out[l] = S;
+    }
+}
+
+__global__ void k_widths(Prob p, float *aDinv_out, float *y_out)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < p.n;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        double S, aDinv, y;
+        line_strength_f64(p, l, &S, &aDinv, &y);
+        aDinv_out[l] = (float)aDinv;
+        y_out[l] = (float)y;
+    }
+}
+
+// Sort support: order-preserving 64-bit keys of the nu0 doubles.
+__global__ void k_sort_keys(const double *nu0, int64_t n, unsigned long long *keys, int64_t *idx)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long b = (unsigned long long)__double_as_longlong(nu0[l]);
+        keys[l] = (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+        idx[l] = l;
+    }
+}
+
+__global__ void k_gather_fields(const hk_lines L, const int64_t *perm, int64_t n, double *nu0,
+                                float *S_ref, float *A, float *g_up, float *E_low, float *gamma,
+                                float *n_T)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        int64_t s = perm[l];
+        nu0[l] = L.nu0[s];
+        if (L.S_ref) S_ref[l] = L.S_ref[s];
+        if (L.A) A[l] = L.A[s];
+        if (L.g_up) g_up[l] = L.g_up[s];
+        E_low[l] = L.E_low[s];
+        gamma[l] = L.gamma_ref[s];
+        n_T[l] = L.n_T[s];
+    }
+}
+
+static inline size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Bytes needed to hold a sorted copy of a line list (plus the permutation).
+size_t sort_bytes(int64_t n, size_t *cub_bytes)
+{
+    size_t tb = 0;
+    cub::DeviceRadixSort::SortPairs((void *)nullptr, tb, (const unsigned long long *)nullptr,
+                                    (unsigned long long *)nullptr, (const int64_t *)nullptr,
+                                    (int64_t *)nullptr, (int64_t)n, 0, 64, (cudaStream_t)0);
+    *cub_bytes = tb;
+    return al(tb) + 2 * al(n * 8) + 2 * al(n * 8) + al(n * 8) + 6 * al(n * 4);
+}
+
+// Builds a sorted copy of `L` in `ws`; fills `S` with device pointers into ws and
+// `perm_out` with sorted-position -> original-index.
+int sort_lines(const hk_lines *L, char *ws, hk_lines *S, int64_t **perm_out, cudaStream_t st)
+{
+    int64_t n = L->n;
+    size_t tb;
+    sort_bytes(n, &tb);
+    char *cur = ws;
+    auto take = [&](size_t b) {
+        char *r = cur;
+        cur += al(b);
+        return r;
+    };
+    void *temp = take(tb);
+    auto *k_in = (unsigned long long *)take(n * 8), *k_out = (unsigned long long *)take(n * 8);
+    auto *i_in = (int64_t *)take(n * 8), *i_out = (int64_t *)take(n * 8);
+    auto *nu0 = (double *)take(n * 8);
+    auto *S_ref = (float *)take(n * 4), *A = (float *)take(n * 4), *g_up = (float *)take(n * 4);
+    auto *E = (float *)take(n * 4), *gam = (float *)take(n * 4), *nT = (float *)take(n * 4);
+    int sms = num_sms();
+    k_sort_keys<<<sms * 4, 256, 0, st>>>(L->nu0, n, k_in, i_in);
+    cudaError_t e = cudaGetLastError();
+    if (e) return fail_cuda(e);
+    e = cub::DeviceRadixSort::SortPairs(temp, tb, k_in, k_out, i_in, i_out, n, 0, 64, st);
+    if (e) return fail_cuda(e);
+    k_gather_fields<<<sms * 4, 256, 0, st>>>(*L, i_out, n, nu0, S_ref, A, g_up, E, gam, nT);
+    if ((e = cudaGetLastError())) return fail_cuda(e);
+    *S = *L;
+    S->nu0 = nu0;
+    S->S_ref = L->S_ref ? S_ref : nullptr;
+    S->A = L->A ? A : nullptr;
+    S->g_up = L->g_up ? g_up : nullptr;
+    S->E_low = E;
+    S->gamma_ref = gam;
+    S->n_T = nT;
+    S->sorted = 1;
+    *perm_out = i_out;
+    return HK_OK;
+}
+
+}  // namespace hk
+
+using namespace hk;
+
+// ============================================================================
+extern "C" {
+
+int hk_version(void) { return 100; }
+
+const char *hk_strerror(int s)
+{
+    switch (s) {
+    case HK_OK: return "ok";
+    case HK_EINVAL: return "invalid argument";
+    case HK_ENOMEM: return "scratch pool or workspace too small";
+    case HK_ECUDA: return "CUDA error";
+    case HK_ETIMEOUT: return "bounded device wait gave up";
+    case HK_ENOTSUP: return "unsupported combination of options";
+    case HK_ERANGE: return "a float sigma output overflowed (use HK_SIGMA_F64)";
+    default: return "unknown status";
+    }
+}
+
+int hk_last_cuda_error(void) { return g_last_cuda; }
+
+int hk_constants(double *out6)
+{
+    if (!out6) return HK_EINVAL;
+    out6[0] = kC;
+    out6[1] = kKB;
+    out6[2] = kH;
+    out6[3] = kAMU;
+    out6[4] = kC2;
+    out6[5] = kPI;
+    return HK_OK;
+}
+
+int hk_release(void)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) {
+        if (it->second.ptr) {
+            cudaError_t e = cudaFree(it->second.ptr);
+            if (e) return fail_cuda(e);
+        }
+        g_pools.erase(it);
+    }
+    return HK_OK;
+}
+
+int hk_count_pairs(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
+                   const hk_opts *opts, int64_t *counts, void *stream)
+{
+    int rc;
+    if ((rc = check_lines(lines, true)) || (rc = check_grid(grid)) || (rc = check_state(state)) ||
+        (rc = check_opts(opts)))
+        return rc;
+    if (!counts) return HK_EINVAL;
+    for (int t = 0; t < 6; ++t) counts[t] = 0;
+    if (lines->n == 0) return HK_OK;
+    char *ws;
+    if ((rc = pool_get(256, &ws))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Prob p = make_prob(lines, state, opts);
+    GridD g = make_grid(grid, opts);
+    if ((rc = count_pairs_run(p, g, (unsigned long long *)ws, st, num_sms()))) return rc;
+    unsigned long long h[6];
+    cudaError_t e = cudaMemcpyAsync(h, ws, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return fail_cuda(e);
+    for (int t = 0; t < 6; ++t) counts[t] = (int64_t)h[t];
+    return HK_OK;
+}
+
+int hk_profile(int mode, double *ms, int64_t *launches)
+{
+    if (mode != 0 && mode != 1) return HK_EINVAL;
+    return gather_profile(mode, ms, launches);
+}
+
+int hk_sync_status(void *stream)
+{
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e) return fail_cuda(e);
+    unsigned *sw = status_word();
+    if (!sw) return HK_ENOMEM;
+    unsigned v = 0;
+    e = cudaMemcpy(&v, sw, sizeof(v), cudaMemcpyDeviceToHost);
+    if (!e && v) e = cudaMemset(sw, 0, sizeof(v));
+    if (e) return fail_cuda(e);
+    if (v & kStatusTimeout) return HK_ETIMEOUT;
+    if (v & kStatusRange) return HK_ERANGE;
+    return HK_OK;
+}
+
+int hk_line_strength(const hk_lines *lines, const hk_state *state, const hk_opts *opts,
+                     double *S_out, void *stream)
+{
+    int rc;
+    if ((rc = check_lines(lines, true)) || (rc = check_state(state)) || (rc = check_opts(opts)))
+        return rc;
+    if (lines->n == 0) return HK_OK;
+    if (!S_out) return HK_EINVAL;
+    Prob p = make_prob(lines, state, opts);
+    k_strength<<<num_sms() * 4, 256, 0, (cudaStream_t)stream>>>(p, S_out);
+    cudaError_t e = cudaGetLastError();
+    return e ? fail_cuda(e) : HK_OK;
+}
+
+int hk_widths(const hk_lines *lines, const hk_state *state, const hk_opts *opts,
+              float *alphaD_inv_out, float *y_out, void *stream)
+{
+    int rc;
+    if ((rc = check_lines(lines, true)) || (rc = check_state(state)) || (rc = check_opts(opts)))
+        return rc;
+    if (lines->n == 0) return HK_OK;
+    if (!alphaD_inv_out || !y_out) return HK_EINVAL;
+    Prob p = make_prob(lines, state, opts);
+    k_widths<<<num_sms() * 4, 256, 0, (cudaStream_t)stream>>>(p, alphaD_inv_out, y_out);
+    cudaError_t e = cudaGetLastError();
+    return e ? fail_cuda(e) : HK_OK;
+}
+
+int hk_voigt_accumulate(const double *nu0, const double *S, const float *alphaD_inv,
+                        const float *y, int64_t n, const hk_grid *grid, double cut,
+                        void *sigma_inout, int precision, void *stream)
+{
+    int rc;
+    if ((rc = check_grid(grid))) return rc;
+    if (n < 0 || !std::isfinite(cut) || (precision != HK_FP32C && precision != HK_FP64))
+        return HK_EINVAL;
+    if (n == 0) return HK_OK;
+    if (!nu0 || !S || !alphaD_inv || !y || !sigma_inout) return HK_EINVAL;
+    Prob p;
+    memset(&p, 0, sizeof(p));
+    p.nu0 = nu0;
+    p.S_pre = S;
+    p.aDinv_pre = alphaD_inv;
+    p.y_pre = y;
+    p.n = n;
+    p.pre = 1;
+    GridD g = make_grid_cut(grid, cut);
+    Tune t = get_tune(precision);
+    size_t need = gather_workspace(1, g.nbins, precision, t.bpt);
+    char *ws;
+    if ((rc = pool_get(need, &ws))) return rc;
+    unsigned *sw = status_word();
+    if (!sw) return HK_ENOMEM;
+    return gather_run(&p, 1, g, precision, t.bpt, t.lmax, sigma_inout, 0, 1, ws, need, sw,
+                      (cudaStream_t)stream, num_sms());
+}
+
+static int cross_section_impl(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
+                              const hk_opts *opts, void *sigma_out, cudaStream_t st, int bpt,
+                              int lmax)
+{
+    int rc;
+    GridD g = make_grid(grid, opts);
+    int prec = opts->precision;
+    const int out_f64 = (opts->flags & HK_SIGMA_F64) ? 1 : 0;
+    if (lines->n == 0) {
+        size_t b = (size_t)grid->nbins * ((prec == HK_FP64 || out_f64) ? 8 : 4);
+        cudaError_t e = cudaMemsetAsync(sigma_out, 0, b, st);
+        return e ? fail_cuda(e) : HK_OK;
+    }
+    size_t need = gather_workspace(1, g.nbins, prec, bpt);
+    size_t sort_need = 0, cub_b = 0;
+    if (!lines->sorted) sort_need = al(sort_bytes(lines->n, &cub_b));
+    char *ws;
+    if ((rc = pool_get(need + sort_need, &ws))) return rc;
+    hk_lines L = *lines;
+    if (!lines->sorted) {
+        int64_t *perm;
+        if ((rc = sort_lines(lines, ws + need, &L, &perm, st))) return rc;
+    }
+    Prob p = make_prob(&L, state, opts);
+    unsigned *sw = status_word();
+    if (!sw) return HK_ENOMEM;
+    return gather_run(&p, 1, g, prec, bpt, lmax, sigma_out, out_f64, 0, ws, need, sw, st,
+                      num_sms());
+}
+
+int hk_cross_section(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
+                     const hk_opts *opts, void *sigma_out, void *stream)
+{
+    int rc;
+    if ((rc = check_lines(lines, true)) || (rc = check_grid(grid)) || (rc = check_state(state)) ||
+        (rc = check_opts(opts)))
+        return rc;
+    if (!sigma_out) return HK_EINVAL;
+    Tune t = get_tune(opts->precision);
+    return cross_section_impl(lines, grid, state, opts, sigma_out, (cudaStream_t)stream, t.bpt,
+                              t.lmax);
+}
+
+int hk_workspace_size(int kind, const hk_lines *species, int nspecies, int nTP,
+                      const hk_grid *grid, const hk_opts *opts, size_t *bytes)
+{
+    int rc;
+    if (!bytes || !species || nspecies <= 0 || nTP <= 0 || (kind != 0 && kind != 1)) return HK_EINVAL;
+    if ((rc = check_grid(grid)) || (rc = check_opts(opts))) return rc;
+    size_t total = 0;
+    if (kind == 0) {
+        Tune t = get_tune(opts->precision);
+        total = gather_workspace(nspecies * nTP, grid->nbins, HK_FP32C, t.bpt);
+        for (int s = 0; s < nspecies; ++s) {
+            if ((rc = check_lines(&species[s], true))) return rc;
+            if (!species[s].sorted && species[s].n > 0) {
+                size_t cb;
+                total += al(sort_bytes(species[s].n, &cb));
+            }
+        }
+    } else {
+        if ((rc = check_lines(&species[0], true))) return rc;
+        total = backward_workspace(species[0].n, nTP, grid->nbins);
+        if (!species[0].sorted && species[0].n > 0) {
+            size_t cb;
+            total += al(sort_bytes(species[0].n, &cb));
+        }
+    }
+    *bytes = total;
+    return HK_OK;
+}
+
+int hk_cross_section_batched(const hk_lines *species, int nspecies, const hk_state *TP, int nTP,
+                             const hk_grid *grid, const hk_opts *opts, void *sigma_out,
+                             void *workspace, size_t ws_bytes, void *stream)
+{
+    int rc;
+    if (!species || nspecies <= 0 || !TP || nTP <= 0 || !sigma_out) return HK_EINVAL;
+    if ((rc = check_grid(grid)) || (rc = check_opts(opts))) return rc;
+    if (opts->precision != HK_FP32C) return HK_ENOTSUP;
+    for (int s = 0; s < nspecies; ++s)
+        if ((rc = check_lines(&species[s], true))) return rc;
+    for (int k = 0; k < nTP; ++k)
+        if ((rc = check_state(&TP[k]))) return rc;
+    size_t need;
+    if ((rc = hk_workspace_size(0, species, nspecies, nTP, grid, opts, &need))) return rc;
+    if (!workspace || ws_bytes < need) return HK_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    Tune t = get_tune(HK_FP32C);
+    size_t gneed = gather_workspace(nspecies * nTP, grid->nbins, HK_FP32C, t.bpt);
+    char *sort_ws = (char *)workspace + gneed;
+    std::vector<hk_lines> L(species, species + nspecies);
+    for (int s = 0; s < nspecies; ++s) {
+        if (!species[s].sorted && species[s].n > 0) {
+            int64_t *perm;
+            if ((rc = sort_lines(&species[s], sort_ws, &L[s], &perm, st))) return rc;
+            size_t cb;
+            sort_ws += al(sort_bytes(species[s].n, &cb));
+        }
+    }
+    std::vector<Prob> probs;
+    probs.reserve((size_t)nspecies * nTP);
+    for (int s = 0; s < nspecies; ++s)
+        for (int k = 0; k < nTP; ++k) probs.push_back(make_prob(&L[s], &TP[k], opts));
+    GridD g = make_grid(grid, opts);
+    unsigned *sw = status_word();
+    if (!sw) return HK_ENOMEM;
+    return gather_run(probs.data(), (int)probs.size(), g, HK_FP32C, t.bpt, t.lmax, sigma_out,
+                      (opts->flags & HK_SIGMA_F64) ? 1 : 0, 0, (char *)workspace, gneed, sw, st,
+                      num_sms());
+}
+
+int hk_cross_section_backward(const hk_lines *lines, const hk_grid *grid, const hk_state *TP,
+                              int nTP, const hk_opts *opts, const float *grad_sigma,
+                              double *dL_dT, double *dL_dP, double *dL_dSref,
+                              double *dL_dgamma_ref, void *workspace, size_t ws_bytes,
+                              void *stream)
+{
+    int rc;
+    if ((rc = check_lines(lines, true)) || (rc = check_grid(grid)) || (rc = check_opts(opts)))
+        return rc;
+    if (!TP || nTP <= 0 || !grad_sigma || !dL_dT || !dL_dP) return HK_EINVAL;
+    if (lines->n > 0 && (!dL_dSref || !dL_dgamma_ref)) return HK_EINVAL;
+    if (lines->s_mode != HK_S_REF) return HK_ENOTSUP;
+    for (int k = 0; k < nTP; ++k)
+        if ((rc = check_state(&TP[k]))) return rc;
+    size_t need;
+    if ((rc = hk_workspace_size(1, lines, 1, nTP, grid, opts, &need))) return rc;
+    if (!workspace || ws_bytes < need) return HK_ENOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bneed = backward_workspace(lines->n, nTP, grid->nbins);
+    hk_lines L = *lines;
+    const int64_t *perm = nullptr;
+    if (!lines->sorted && lines->n > 0) {
+        int64_t *pm;
+        if ((rc = sort_lines(lines, (char *)workspace + bneed, &L, &pm, st))) return rc;
+        perm = pm;
+    }
+    std::vector<Prob> probs;
+    std::vector<double> dlnQ(nTP), T(nTP), P(nTP);
+    for (int k = 0; k < nTP; ++k) {
+        probs.push_back(make_prob(&L, &TP[k], opts));
+        dlnQ[k] = TP[k].dlnQ_dT;
+        T[k] = TP[k].T;
+        P[k] = TP[k].P;
+    }
+    GridD g = make_grid(grid, opts);
+    return backward_run(probs.data(), nTP, g, grad_sigma, dlnQ.data(), T.data(), P.data(), dL_dT,
+                        dL_dP, dL_dSref, dL_dgamma_ref, perm, (char *)workspace, bneed, st,
+                        num_sms());
+}
+
+int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
+                const hk_opts *opts, void *stream)
+{
+    int rc;
+    if ((rc = check_lines(lines, true)) || (rc = check_grid(grid)) || (rc = check_state(state)) ||
+        (rc = check_opts(opts)))
+        return rc;
+    if (lines->n == 0) return HK_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int prec = opts->precision;
+    const int bpts_f[] = {2, 4, 8};
+    const int bpts_d[] = {2};
+    const int lmaxs[] = {4096, 16384, 65536};
+    size_t out_b = (size_t)grid->nbins * 8;
+    // the output buffer lives in its own cudaMalloc (the pool is used by the runs)
+    void *out = nullptr;
+    if (cudaMalloc(&out, out_b) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return HK_ENOMEM;
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    Tune best;
+    float best_ms = 1e30f;
+    const int *bp = prec == HK_FP64 ? bpts_d : bpts_f;
+    int nb = prec == HK_FP64 ? 1 : 3;
+    for (int i = 0; i < nb && rc == HK_OK; ++i)
+        for (int j = 0; j < 3 && rc == HK_OK; ++j) {
+            // one warm-up, then one timed run
+            rc = cross_section_impl(lines, grid, state, opts, out, st, bp[i], lmaxs[j]);
+            if (rc) break;
+            cudaEventRecord(e0, st);
+            rc = cross_section_impl(lines, grid, state, opts, out, st, bp[i], lmaxs[j]);
+            cudaEventRecord(e1, st);
+            if (rc) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = fail_cuda(cudaGetLastError());
+                break;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best.bpt = bp[i];
+                best.lmax = lmaxs[j];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    cudaFree(out);
+    if (rc) return rc;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[{dev, prec}] = best;
+    return HK_OK;
+}
+
+}  // extern "C"

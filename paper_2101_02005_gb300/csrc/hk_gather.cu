@@ -1,0 +1,576 @@
+// hk_gather.cu -- the Voigt sum sigma_i = sum_l S_l phi_l(nu_i) on sm_103a.
+//
+// Design (GB300-first; the paper's line-parallel scatter with rotated
+// shared-memory writes, Sect. 2.4.4, is prior art and not used):
+//
+// * Work items.  The grid is cut into tiles of NWARPS*32*BPT bins.  A tile's
+//   candidate lines are a contiguous range of the nu0-sorted list (bisection
+//   on nu0 with the cut), split into items of at most `lmax` lines.  Items of
+//   every (problem, tile) are numbered by an exclusive scan; one persistent
+//   launch pulls items from an atomic counter, so uneven line density
+//   (log-normal windows) and many problems (species x T x P) balance across
+//   the 152 SMs.
+// * Bin-parallel gather.  Each lane owns BPT bins of its warp's slice of the
+//   tile (lane-strided, so neighbouring lanes hold neighbouring bins and see
+//   the same Faddeeva band).  Lines are staged in shared memory in chunks of
+//   CHUNK; their parameters (bin geometry, S, widths) are computed once per
+//   chunk by one thread per line and read back as warp-wide broadcasts.
+// * Accumulation.  FP32C: FP32 partial sums per lane, folded every FLUSH
+//   lines into a (hi, lo) two-sum pair; at the end of the item one FP64
+//   atomicAdd per bin into a per-problem FP64 accumulator (the final
+//   cross-tile sum is FP64).  FP64: double accumulators and atomics.
+// * Exact cut.  Membership of a bin is decided by integer compare against the
+//   line's [lo, hi] bin range, itself decided in FP64 by the predicate
+//   |k - r| <= W (see line_geometry) -- the same decision as the oracle's.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "hk_internal.cuh"
+#include "hk_launch.h"
+
+namespace hk {
+
+constexpr int NWARPS = 8;
+constexpr int NTHREADS = NWARPS * 32;
+constexpr int CHUNK = NTHREADS;  // lines staged per pass: one prologue thread per line
+constexpr int FLUSH = 32;        // FP32 lines per two-sum fold
+
+template <typename R> struct LineT {
+    R b, r, y, s;
+    int i0, lo, hi, pad;
+};
+
+// ---- scale prepass ---------------------------------------------------------------
+// FP32C sums S * alphaD_inv / sqrt(pi) * Re w scaled by 2^-scale so that the
+// largest value any line puts into any bin is about 1: far from overflow even
+// after summing 1e9 lines, and with the 1e-10 dynamic range the parity bar
+// looks at far from the float denormals.  A line's largest sampled value is
+// at its nearest bin, x_n = |r_n| b (r_n in [-1/2, 1/2]); a narrow line whose
+// centre falls between bins never reaches its peak, so the peak is not used.
+// Re w(x, y) <= min(1, exp(-x^2) + y / (sqrt(pi) x^2)) bounds it within a
+// small factor, which is all the exponent needs.
+__device__ __forceinline__ int sampled_peak_exp2(float x_n, float y)
+{
+    float X = x_n * x_n;
+    float B = expf(-X) + (float)kInvSqrtPi * y / X;  // X = 0 gives +inf -> 1
+    B = fminf(B, 1.0f);
+    return B > 0.0f ? ilogbf(B) : INT_MIN / 2;
+}
+
+__global__ void k_scale_prepass(const Prob *__restrict__ probs, int nprob, GridD g)
+{
+    int p = blockIdx.y;
+    if (p >= nprob) return;
+    const Prob &pr = probs[p];
+    const double nu_lo = g.nu_min - g.cut - g.dnu;
+    const double nu_hi = g.nu_min + (double)g.nbins * g.dnu + g.cut + g.dnu;
+    int emax = INT_MIN;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pr.n;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const double nu0 = pr.nu0[l];
+        if (!(nu0 > 0.0) || (g.W > 0.0 && (nu0 < nu_lo || nu0 > nu_hi))) continue;
+        // approximate nearest-bin offset (float is enough for an exponent)
+        float u = (float)(nu0 - g.nu_min) * (float)g.inv_dnu;
+        float rn = fabsf(u - rintf(u));
+        int e;
+        if (pr.pre) {
+            double v = pr.S_pre[l] * (double)pr.aDinv_pre[l] * kInvSqrtPi;
+            float b = (float)g.dnu * pr.aDinv_pre[l];
+            e = v > 0.0 ? ilogb(v) + sampled_peak_exp2(rn * b, pr.y_pre[l]) : INT_MIN;
+        } else {
+            float P, aDinv, y;
+            int e2;
+            line_strength_f32(pr, l, &P, &e2, &aDinv, &y);
+            float b = (float)g.dnu * aDinv;
+            e = P > 0.0f ? ilogbf(P) + e2 + sampled_peak_exp2(rn * b, y) : INT_MIN;
+        }
+        emax = max(emax, e);
+    }
+    for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    if ((threadIdx.x & 31) == 0 && emax != INT_MIN) atomicMax(pr.scale_exp, emax);
+}
+
+// ---- tile line ranges and item counts ---------------------------------------
+__device__ __forceinline__ int64_t lower_bound_nu(const double *nu, int64_t n, double v)
+{
+    int64_t a = 0, b = n;
+    while (a < b) {
+        int64_t m = (a + b) >> 1;
+        if (nu[m] < v) a = m + 1; else b = m;
+    }
+    return a;
+}
+__device__ __forceinline__ int64_t upper_bound_nu(const double *nu, int64_t n, double v)
+{
+    int64_t a = 0, b = n;
+    while (a < b) {
+        int64_t m = (a + b) >> 1;
+        if (nu[m] <= v) a = m + 1; else b = m;
+    }
+    return a;
+}
+
+__global__ void k_tile_ranges(const Prob *__restrict__ probs, int nprob, GridD g, int tile_bins,
+                              int64_t ntiles, int lmax, int64_t *tile_lb, int64_t *tile_le,
+                              int64_t *counts)
+{
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nprob * ntiles) return;
+    int p = (int)(idx / ntiles);
+    int64_t t = idx - (int64_t)p * ntiles;
+    const Prob &pr = probs[p];
+    int64_t lb = 0, le = pr.n;
+    if (g.W > 0.0) {
+        double lo_nu = g.nu_min + (double)(t * tile_bins) * g.dnu - g.cut - 2.0 * g.dnu;
+        double hi_nu = g.nu_min + (double)(t * tile_bins + tile_bins - 1) * g.dnu + g.cut + 2.0 * g.dnu;
+        lb = lower_bound_nu(pr.nu0, pr.n, lo_nu);
+        le = upper_bound_nu(pr.nu0, pr.n, hi_nu);
+    }
+    tile_lb[idx] = lb;
+    tile_le[idx] = le;
+    counts[idx] = le > lb ? (le - lb + lmax - 1) / lmax : 0;
+}
+
+// Exclusive scan of counts[0..m) into off[0..m] (off[m] = total); one block.
+__global__ void k_scan(const int64_t *counts, int64_t m, int64_t *off)
+{
+    __shared__ int64_t part[1024];
+    int tid = threadIdx.x;
+    int64_t seg = (m + blockDim.x - 1) / blockDim.x;
+    int64_t a = tid * seg, b = min(m, a + seg);
+    int64_t s = 0;
+    for (int64_t i = a; i < b; ++i) s += counts[i];
+    part[tid] = s;
+    __syncthreads();
+    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+        int64_t v = tid >= o ? part[tid - o] : 0;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    int64_t run = tid ? part[tid - 1] : 0;
+    for (int64_t i = a; i < b; ++i) {
+        off[i] = run;
+        run += counts[i];
+    }
+    if (tid == blockDim.x - 1) off[m] = part[tid];
+}
+
+// ---- the gather ---------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void stage_line(const Prob &pr, const GridD &g, int64_t l, int scale,
+                                           LineT<R> *out, double *nu_out)
+{
+    double nu0 = pr.nu0[l];
+    int i0, lo, hi;
+    double r;
+    bool any = line_geometry(nu0, g, &i0, &r, &lo, &hi);
+    LineT<R> q;
+    int c;
+    double rn;
+    nearest_bin(i0, r, &c, &rn);
+    q.i0 = c;
+    q.lo = lo;
+    q.hi = hi;
+    q.r = (R)rn;
+    q.pad = 0;
+    if (!any) {
+        q.b = R(1);
+        q.y = R(1);
+        q.s = R(0);
+    } else if (sizeof(R) == 4) {
+        float aDinv, y, P;
+        int e2;
+        if (pr.pre) {
+            aDinv = pr.aDinv_pre[l];
+            y = pr.y_pre[l];
+            double v = pr.S_pre[l] * (double)aDinv * kInvSqrtPi;
+            P = (float)ldexp(v, -scale);
+            e2 = 0;
+            q.s = (R)P;
+        } else {
+            line_strength_f32(pr, l, &P, &e2, &aDinv, &y);
+            q.s = (R)ldexpf(P, e2 - scale);
+        }
+        q.b = (R)((float)g.dnu * aDinv);
+        q.y = (R)y;
+    } else {
+        double S, aDinv, y;
+        if (pr.pre) {
+            S = pr.S_pre[l];
+            aDinv = (double)pr.aDinv_pre[l];
+            y = (double)pr.y_pre[l];
+        } else {
+            line_strength_f64(pr, l, &S, &aDinv, &y);
+        }
+        q.s = (R)(S * aDinv * kInvSqrtPi);
+        q.b = (R)(g.dnu * aDinv);
+        q.y = (R)y;
+    }
+    *out = q;
+    *nu_out = nu0;
+}
+
+// Contribution s * Re w(x + iy) of one (line, bin) pair; sy = s * y / sqrt(pi).
+template <typename R> __device__ __forceinline__ R pair_value(R x, R y, R Y, R s, R sy)
+{
+    R X = x * x;
+    R r2 = X + Y;
+    if (r2 >= BandLimits<R>::gh3) {
+        if (r2 >= BandLimits<R>::gh2) return sy * gh1_F<R>(r2);
+        return sy * gh2_F<R>(X, Y, r2);
+    }
+    if (r2 >= BandLimits<R>::gh4) return sy * gh3_F<R>(X, Y, r2);
+    if (r2 >= BandLimits<R>::core) return sy * gh4_F<R>(X, Y, r2);
+    return s * core_re<R>(x, y);
+}
+
+template <typename R, int BPT>
+__global__ void __launch_bounds__(NTHREADS, 2)
+    k_gather(const Prob *__restrict__ probs, GridD g, int64_t ntiles, int64_t m,
+             const int64_t *__restrict__ item_off,
+             const int64_t *__restrict__ tile_lb, const int64_t *__restrict__ tile_le, int lmax,
+             unsigned long long *counter)
+{
+    constexpr int TILE = NWARPS * 32 * BPT;
+    __shared__ LineT<R> sl[CHUNK];
+    __shared__ double snu[CHUNK];
+    __shared__ long long s_item, s_pt, s_lb, s_le;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (;;) {
+        if (tid == 0) {
+            unsigned long long it = atomicAdd(counter, 1ull);
+            long long item = (long long)it;
+            // item_off has m + 1 entries; the last one is the number of items
+            long long total = item_off[m];
+            if (item >= total) {
+                s_item = -1;
+            } else {
+                long long a = 0, b = m;  // largest pt with item_off[pt] <= item
+                while (b - a > 1) {
+                    long long c = (a + b) >> 1;
+                    if (item_off[c] <= item) a = c; else b = c;
+                }
+                long long chunk = item - item_off[a];
+                long long lb = tile_lb[a] + chunk * lmax;
+                long long le = min((long long)tile_le[a], lb + lmax);
+                s_item = item;
+                s_pt = a;
+                s_lb = lb;
+                s_le = le;
+            }
+        }
+        __syncthreads();
+        if (s_item < 0) break;
+        const int64_t pt = s_pt;
+        const int p = (int)(pt / ntiles);
+        const int64_t t = pt - (int64_t)p * ntiles;
+        const int64_t l_begin = s_lb, l_end = s_le;
+        const Prob &pr = probs[p];
+        const int scale = (sizeof(R) == 4) ? *pr.scale_exp : 0;
+
+        const int wb0 = (int)(t * TILE) + warp * 32 * BPT;  // first bin of this warp
+        const double wnu_lo = g.nu_min + (double)wb0 * g.dnu - g.cut - 2.0 * g.dnu;
+        const double wnu_hi = g.nu_min + (double)(wb0 + 32 * BPT - 1) * g.dnu + g.cut + 2.0 * g.dnu;
+
+        R acc[BPT], shi[BPT], slo[BPT];
+#pragma unroll
+        for (int j = 0; j < BPT; ++j) acc[j] = shi[j] = slo[j] = R(0);
+        int nsince = 0;
+
+        for (int64_t cs = l_begin; cs < l_end; cs += CHUNK) {
+            __syncthreads();
+            const int nl = (int)min((int64_t)CHUNK, l_end - cs);
+            if (tid < nl) stage_line<R>(pr, g, cs + tid, scale, &sl[tid], &snu[tid]);
+            __syncthreads();
+            // this warp's candidate lines inside the chunk (bisection on nu0)
+            int a = 0, b = nl;
+            if (g.W > 0.0) {
+                int lo = 0, hi = nl;
+                while (lo < hi) {
+                    int m = (lo + hi) >> 1;
+                    if (snu[m] < wnu_lo) lo = m + 1; else hi = m;
+                }
+                a = lo;
+                hi = nl;
+                while (lo < hi) {
+                    int m = (lo + hi) >> 1;
+                    if (snu[m] <= wnu_hi) lo = m + 1; else hi = m;
+                }
+                b = lo;
+            }
+            for (int l = a; l < b; ++l) {
+                const LineT<R> q = sl[l];
+                if (q.hi < wb0 || q.lo > wb0 + 32 * BPT - 1) continue;  // warp-uniform
+                // x = (k - r) b for the integer bin offset k = bin - i0: formed as
+                // fma(k, b, -r b) with k exact, one rounding, so a bin next to the
+                // centre keeps full relative precision whatever the lane's first bin.
+                const R kf0 = (R)(wb0 + lane - q.i0);
+                const R rb = q.r * q.b;
+                const R y = q.y, Y = y * y;
+                const R sy = q.s * y * R(kInvSqrtPi);
+                const unsigned span = (unsigned)(q.hi - q.lo);
+                const int kk = wb0 + lane - q.lo;
+#pragma unroll
+                for (int j = 0; j < BPT; ++j) {
+                    const bool inr = (unsigned)(kk + 32 * j) <= span;
+                    const R x = fma(kf0 + R(32 * j), q.b, -rb);
+                    const R v = pair_value<R>(x, y, Y, q.s, sy);
+                    acc[j] += inr ? v : R(0);
+                }
+                if (sizeof(R) == 4 && ++nsince == FLUSH) {
+                    nsince = 0;
+#pragma unroll
+                    for (int j = 0; j < BPT; ++j) {
+                        float sh, e;
+                        two_sum((float)shi[j], (float)acc[j], &sh, &e);
+                        shi[j] = (R)sh;
+                        slo[j] += (R)e;
+                        acc[j] = R(0);
+                    }
+                }
+            }
+        }
+        // fold and publish
+#pragma unroll
+        for (int j = 0; j < BPT; ++j) {
+            const int64_t bin = (int64_t)wb0 + lane + 32 * j;
+            double tot;
+            if (sizeof(R) == 4) {
+                float sh, e;
+                two_sum((float)shi[j], (float)acc[j], &sh, &e);
+                tot = (double)sh + ((double)slo[j] + (double)e);
+            } else {
+                tot = (double)acc[j];
+            }
+            if (bin < g.nbins && tot != 0.0) atomicAdd(pr.acc + bin, tot);
+        }
+        __syncthreads();
+    }
+}
+
+// ---- finalize: sigma from the scaled FP64 accumulator --------------------------
+// A scale slot still holding its fill value (no line with S > 0) means an
+// all-zero accumulator.
+constexpr int kNoScale = (int)0x80808080;
+
+template <typename O>
+__global__ void k_finalize(const Prob *__restrict__ probs, int nprob, int64_t nbins, O *out,
+                           int accumulate)
+{
+    int p = blockIdx.y;
+    const double *acc = probs[p].acc;
+    int sc = *probs[p].scale_exp;
+    if (sc == kNoScale) sc = 0;
+    O *o = out + (int64_t)p * nbins;
+    bool over = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nbins;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v = ldexp(acc[i], sc);
+        if (accumulate) v += (double)o[i];
+        O ov = (O)v;
+        over |= isinf((double)ov) && !isinf(v);
+        o[i] = ov;
+    }
+    if (over) atomicOr(probs[p].status, kStatusRange);
+}
+
+// ---- pair / band counts (instrumentation) --------------------------------------
+__global__ void k_count_pairs(Prob p, GridD g, unsigned long long *counts)
+{
+    unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < p.n;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        int i0, lo, hi;
+        double r;
+        if (!line_geometry(p.nu0[l], g, &i0, &r, &lo, &hi)) continue;
+        double S, aDinv, y;
+        line_strength_f64(p, l, &S, &aDinv, &y);
+        double b = g.dnu * aDinv;
+        double klo = (double)(lo - i0), khi = (double)(hi - i0);
+        c[0] += (unsigned long long)(hi - lo + 1);
+        // pairs with r2 < R2: |k - r| < sqrt(R2 - y^2) / b
+        const double R2[4] = {1.5e6, 2500.0, 200.0, 64.0};
+        unsigned long long inside[4];
+        for (int t = 0; t < 4; ++t) {
+            double D2 = R2[t] - y * y;
+            if (D2 <= 0.0) { inside[t] = 0; continue; }
+            double D = sqrt(D2) / b;
+            double a = fmax(klo, floor(r - D) + 1.0), e = fmin(khi, ceil(r + D) - 1.0);
+            inside[t] = e >= a ? (unsigned long long)(e - a + 1.0) : 0ull;
+        }
+        unsigned long long tot = (unsigned long long)(hi - lo + 1);
+        c[1] += tot - inside[0];
+        c[2] += inside[0] - inside[1];
+        c[3] += inside[1] - inside[2];
+        c[4] += inside[2] - inside[3];
+        c[5] += inside[3];
+    }
+    for (int t = 0; t < 6; ++t) {
+        unsigned long long v = c[t];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(counts + t, v);
+    }
+}
+
+int count_pairs_run(const Prob &p, const GridD &g, unsigned long long *counts_d, cudaStream_t st,
+                    int num_sms)
+{
+    cudaError_t e = cudaMemsetAsync(counts_d, 0, 6 * sizeof(unsigned long long), st);
+    if (e) return fail_cuda(e);
+    k_count_pairs<<<num_sms * 4, 256, 0, st>>>(p, g, counts_d);
+    if ((e = cudaGetLastError())) return fail_cuda(e);
+    return HK_OK;
+}
+
+// ---- launch profiling (instrumentation) -----------------------------------------
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+static std::vector<cudaEvent_t> g_prof_ev;  // begin, end, begin, end, ...
+
+void gather_profile_record(cudaStream_t st, bool begin)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    if (!begin && g_prof_ev.size() % 2 == 0) return;
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return;
+    }
+    cudaEventRecord(ev, st);
+    g_prof_ev.push_back(ev);
+}
+
+int gather_profile(int mode, double *ms, int64_t *launches)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    double tot = 0.0;
+    int64_t n = 0;
+    int rc = HK_OK;
+    for (size_t i = 0; i + 1 < g_prof_ev.size(); i += 2) {
+        cudaError_t e = cudaEventSynchronize(g_prof_ev[i + 1]);
+        float t = 0.0f;
+        if (!e) e = cudaEventElapsedTime(&t, g_prof_ev[i], g_prof_ev[i + 1]);
+        if (e) rc = fail_cuda(e);
+        tot += t;
+        ++n;
+    }
+    for (cudaEvent_t ev : g_prof_ev) cudaEventDestroy(ev);
+    g_prof_ev.clear();
+    g_prof_on = (mode == 1);
+    if (ms) *ms = mode == 1 ? 0.0 : tot;
+    if (launches) *launches = mode == 1 ? 0 : n;
+    return rc;
+}
+
+// ---- host side ----------------------------------------------------------------
+
+int gather_tile_bins(int precision, int bpt) { return NWARPS * 32 * (precision == 1 ? 2 : bpt); }
+
+size_t gather_workspace(int nprob, int64_t nbins, int precision, int bpt)
+{
+    int64_t tb = gather_tile_bins(precision, bpt);
+    int64_t ntiles = (nbins + tb - 1) / tb;
+    int64_t m = (int64_t)nprob * ntiles;
+    size_t bytes = 0;
+    auto add = [&](size_t b) { bytes += (b + 255) & ~(size_t)255; };
+    add(sizeof(Prob) * nprob);
+    add(sizeof(int) * nprob);
+    add(sizeof(int64_t) * m);       // tile_lb
+    add(sizeof(int64_t) * m);       // tile_le
+    add(sizeof(int64_t) * m);       // counts
+    add(sizeof(int64_t) * (m + 1)); // item_off
+    add(sizeof(unsigned long long) * 2);
+    if (precision == 0) add(sizeof(double) * (size_t)nprob * nbins);
+    return bytes;
+}
+
+int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt, int lmax,
+               void *out, int out_f64, int accumulate, char *ws, size_t ws_bytes,
+               unsigned *status_d, cudaStream_t st, int num_sms)
+{
+    int64_t tb = gather_tile_bins(precision, bpt);
+    int64_t ntiles = (g.nbins + tb - 1) / tb;
+    int64_t m = (int64_t)nprob * ntiles;
+    char *cur = ws;
+    auto take = [&](size_t b) {
+        char *r = cur;
+        cur += (b + 255) & ~(size_t)255;
+        return r;
+    };
+    Prob *probs_d = (Prob *)take(sizeof(Prob) * nprob);
+    int *scales = (int *)take(sizeof(int) * nprob);
+    int64_t *tile_lb = (int64_t *)take(sizeof(int64_t) * m);
+    int64_t *tile_le = (int64_t *)take(sizeof(int64_t) * m);
+    int64_t *counts = (int64_t *)take(sizeof(int64_t) * m);
+    int64_t *item_off = (int64_t *)take(sizeof(int64_t) * (m + 1));
+    unsigned long long *counter = (unsigned long long *)take(sizeof(unsigned long long) * 2);
+    // counter[0]: next work item of the persistent gather
+    double *acc = nullptr;
+    if (precision == 0) acc = (double *)take(sizeof(double) * (size_t)nprob * g.nbins);
+    if ((size_t)(cur - ws) > ws_bytes) return HK_ENOMEM;
+
+    for (int p = 0; p < nprob; ++p) {
+        probs_h[p].status = status_d;
+        probs_h[p].scale_exp = scales + p;
+        if (precision == 0) probs_h[p].acc = acc + (size_t)p * g.nbins;
+        else probs_h[p].acc = (double *)out + (size_t)p * g.nbins;
+    }
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(probs_d, probs_h, sizeof(Prob) * nprob, cudaMemcpyHostToDevice, st)))
+        return fail_cuda(e);
+    if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long) * 2, st))) return fail_cuda(e);
+    if (precision == 0) {
+        if ((e = cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)nprob * g.nbins, st)))
+            return fail_cuda(e);
+        // INT_MIN in every scale slot: 0x80 bytes give 0x80808080 < any real exponent
+        if ((e = cudaMemsetAsync(scales, 0x80, sizeof(int) * nprob, st))) return fail_cuda(e);
+        dim3 grid(num_sms * 2, nprob);
+        k_scale_prepass<<<grid, 256, 0, st>>>(probs_d, nprob, g);
+        if ((e = cudaGetLastError())) return fail_cuda(e);
+    } else if (!accumulate) {
+        if ((e = cudaMemsetAsync(out, 0, sizeof(double) * (size_t)nprob * g.nbins, st)))
+            return fail_cuda(e);
+    }
+    {
+        int64_t blocks = (m + 255) / 256;
+        k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(probs_d, nprob, g, (int)tb, ntiles, lmax,
+                                                        tile_lb, tile_le, counts);
+        if ((e = cudaGetLastError())) return fail_cuda(e);
+        k_scan<<<1, 1024, 0, st>>>(counts, m, item_off);
+        if ((e = cudaGetLastError())) return fail_cuda(e);
+    }
+    {
+        dim3 grid(num_sms * 2);
+        gather_profile_record(st, true);
+        if (precision == 0) {
+            switch (bpt) {
+            case 2: k_gather<float, 2><<<grid, NTHREADS, 0, st>>>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter); break;
+            case 8: k_gather<float, 8><<<grid, NTHREADS, 0, st>>>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter); break;
+            default: k_gather<float, 4><<<grid, NTHREADS, 0, st>>>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter); break;
+            }
+        } else {
+            k_gather<double, 2><<<grid, NTHREADS, 0, st>>>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter);
+        }
+        if ((e = cudaGetLastError())) return fail_cuda(e);
+        gather_profile_record(st, false);
+    }
+    if (precision == 0) {
+        dim3 grid(num_sms * 4, nprob);
+        if (out_f64)
+            k_finalize<double><<<grid, 256, 0, st>>>(probs_d, nprob, g.nbins, (double *)out, accumulate);
+        else
+            k_finalize<float><<<grid, 256, 0, st>>>(probs_d, nprob, g.nbins, (float *)out, accumulate);
+        if ((e = cudaGetLastError())) return fail_cuda(e);
+    }
+    return HK_OK;
+}
+
+}  // namespace hk

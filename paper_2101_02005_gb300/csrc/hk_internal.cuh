@@ -1,0 +1,355 @@
+// hk_internal.cuh -- device-side building blocks of libhk (sm_103a).
+//
+// * physical constants (the device copy; a test checks them against the
+//   values printed in Sect. 2.2 / 2.2.2 of arXiv:2101.02005);
+// * the banded Faddeeva evaluator Re w(x + iy) used by every kernel;
+// * the per-line prologue: bin geometry (integer centre bin, remainder, cut
+//   range) and the scaled strength S * alpha_D^-1 / sqrt(pi).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hk {
+
+// ---- constants ------------------------------------------------------------
+constexpr double kC = 2.99792458e10;      // cm/s            (Sect. 2.2.2, Eq. S)
+constexpr double kKB = 1.3806489e-16;     // erg/K           (Sect. 2.2, Eq. gammaD)
+constexpr double kH = 6.62606957e-27;     // erg s, CODATA 2010 (the paper prints no h)
+constexpr double kAMU = 1.660538921e-24;  // g, CODATA 2010
+constexpr double kPI = 3.14159265358979323846;
+constexpr double kC2 = kH * kC / kKB;     // second radiation constant, cm K
+constexpr double kInvSqrtPi = 0.5641895835477563;
+constexpr double kInvPi = 0.3183098861837907;
+constexpr double kInvLn2 = 1.4426950408889634;
+
+// ---- Faddeeva function: banded evaluation of Re w(x + iy), y >= 0 ----------
+//
+// The a-u plane split of Sect. 2.2.3 (Table regions) is prior art; the bands
+// here are chosen so that every band meets ~1e-6 relative error on Re w in
+// FP32, including y -> 0 where Re w = exp(-x^2) + O(y):
+//
+//   r2 = x^2 + y^2      method                                  rel. error
+//   r2 >= 1.5e6         1-node Gauss-Hermite  y / (sqrt(pi) r2)   1.0e-6
+//   2500 <= r2 < 1.5e6  2-node Gauss-Hermite                      4e-7
+//   200  <= r2 < 2500   3-node Gauss-Hermite                      7e-7
+//   64   <= r2 < 200    4-node Gauss-Hermite                      1e-6
+//   r2 < 64             trapezoid on (i/pi) int e^{-t^2}/(z-t) dt with
+//                       step 1/2, |t| <= 5.75, plus the pole correction
+//                       2 e^{-z^2}/(1 -/+ e^{-2 pi i z/h}) and a half-step
+//                       shift of the nodes when x is near one
+//                       (Chiarella & Reichel 1968; Matta & Reichel 1971)
+//
+// An n-node Gauss-Hermite rule applied to w = (i/pi) int e^{-t^2}/(z - t) dt
+// gives, for symmetric node pairs +-t_j with normalised weights W_j
+// (sum of all W = 1) and tau_j = t_j^2,
+//   Re w = (y / sqrt(pi)) [ sum_pairs 2 W_j (r2 + tau_j) / |z^2 - tau_j|^2 + W_0 / r2 ],
+//   |z^2 - tau|^2 = (x^2 - y^2 - tau)^2 + 4 x^2 y^2,
+// a sum of positive terms: relative accuracy survives y -> 0.
+// The GH functions below return the bracket F, so Re w = y F / sqrt(pi).
+
+enum Band : int { kBandGH1 = 0, kBandGH2 = 1, kBandGH3 = 2, kBandGH4 = 3, kBandCore = 4 };
+
+template <typename R> struct BandLimits {
+    static constexpr R core = R(64), gh4 = R(200), gh3 = R(2500), gh2 = R(1.5e6);
+};
+
+template <typename R> __device__ __forceinline__ R gh1_F(R r2) { return R(1) / r2; }
+
+// 2 nodes: t = +-1/sqrt(2), W = 1/2 each -> 2W = 1.
+template <typename R> __device__ __forceinline__ R gh2_F(R X, R Y, R r2)
+{
+    R a = X - (Y + R(0.5));
+    R d = a * a + X * (R(4) * Y);
+    return (r2 + R(0.5)) / d;
+}
+
+// 3 nodes: t = 0 (W0 = 2/3) and +-sqrt(3/2) (W = 1/6 each).
+template <typename R> __device__ __forceinline__ R gh3_F(R X, R Y, R r2)
+{
+    R a = X - (Y + R(1.5));
+    R d = a * a + X * (R(4) * Y);
+    // (2/3)/r2 + (1/3)(r2 + 3/2)/d over a common denominator
+    return (R(2.0 / 3.0) * d + R(1.0 / 3.0) * (r2 + R(1.5)) * r2) / (r2 * d);
+}
+
+// 4 nodes: tau = (3 -+ sqrt 6)/2, W = (3 +- sqrt 6)/12.
+template <typename R> __device__ __forceinline__ R gh4_F(R X, R Y, R r2)
+{
+    const R ta = R(0.27525512860841106), tb = R(2.724744871391589);
+    const R wa = R(2 * 0.4541241452319315), wb = R(2 * 0.04587585476806851);
+    R a1 = X - (Y + ta), a2 = X - (Y + tb);
+    R fy = X * (R(4) * Y);
+    R d1 = a1 * a1 + fy, d2 = a2 * a2 + fy;
+    return (wa * (r2 + ta) * d2 + wb * (r2 + tb) * d1) / (d1 * d2);
+}
+
+template <typename R> struct Math;
+template <> struct Math<float> {
+    static __device__ __forceinline__ float exp_(float a) { return expf(a); }
+    static __device__ __forceinline__ float expm1_(float a) { return expm1f(a); }
+    static __device__ __forceinline__ void sincos_(float a, float *s, float *c) { sincosf(a, s, c); }
+    static __device__ __forceinline__ void sincospi_(float a, float *s, float *c) { sincospif(a, s, c); }
+    static __device__ __forceinline__ float floor_(float a) { return floorf(a); }
+    static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+};
+template <> struct Math<double> {
+    static __device__ __forceinline__ double exp_(double a) { return exp(a); }
+    static __device__ __forceinline__ double expm1_(double a) { return expm1(a); }
+    static __device__ __forceinline__ void sincos_(double a, double *s, double *c) { sincos(a, s, c); }
+    static __device__ __forceinline__ void sincospi_(double a, double *s, double *c) { sincospi(a, s, c); }
+    static __device__ __forceinline__ double floor_(double a) { return floor(a); }
+    static __device__ __forceinline__ double div_(double a, double b) { return a / b; }
+};
+
+// Trapezoid nodes t = n/2 (W0) and (n + 1/2)/2 (W1), n = -11 .. 11; weights e^{-t^2}.
+#define HK_TRAP_W0                                                                           \
+    {7.28772409581969219e-14, 1.38879438649640209e-11, 1.60522805518561165e-09,              \
+     1.12535174719259116e-07, 4.78511739212900875e-06, 1.23409804086679561e-04,              \
+     1.93045413622770930e-03, 1.83156388887341787e-02, 1.05399224561864333e-01,              \
+     3.67879441171442334e-01, 7.78800783071404878e-01, 1.00000000000000000e+00,              \
+     7.78800783071404878e-01, 3.67879441171442334e-01, 1.05399224561864333e-01,              \
+     1.83156388887341787e-02, 1.93045413622770930e-03, 1.23409804086679561e-04,              \
+     4.78511739212900875e-06, 1.12535174719259116e-07, 1.60522805518561165e-09,              \
+     1.38879438649640209e-11, 7.28772409581969219e-14}
+#define HK_TRAP_W1                                                                           \
+    {1.07092323825080766e-12, 1.58939100945163677e-10, 1.43072419185676882e-08,              \
+     7.81148940830449097e-07, 2.58681002226541202e-05, 5.19574682154838445e-04,              \
+     6.32971542748574697e-03, 4.67706223839589805e-02, 2.09611387151097811e-01,              \
+     5.69782824730923010e-01, 9.39413062813475808e-01, 9.39413062813475808e-01,              \
+     5.69782824730923010e-01, 2.09611387151097811e-01, 4.67706223839589805e-02,              \
+     6.32971542748574697e-03, 5.19574682154838445e-04, 2.58681002226541202e-05,              \
+     7.81148940830449097e-07, 1.43072419185676882e-08, 1.58939100945163677e-10,              \
+     1.07092323825080766e-12, 4.37661850287085020e-15}
+
+// Re w(x + iy) for r2 < 64 (any x sign; uses |x|).
+template <typename R> __device__ __forceinline__ R core_re(R x, R y)
+{
+    constexpr double w0[23] = HK_TRAP_W0;
+    constexpr double w1[23] = HK_TRAP_W1;
+    R ax = x < R(0) ? -x : x;
+    R Y = y * y;
+    R u = ax * R(2);                      // x / h, h = 1/2
+    R fr = u - Math<R>::floor_(u);
+    bool sh = !(fr > R(0.25) && fr < R(0.75));  // x within h/4 of a node: shift lattice
+    R off = sh ? R(0.5) : R(0);
+    R s = R(0);
+#pragma unroll
+    for (int n = -11; n <= 11; ++n) {
+        R t = (R(n) + off) * R(0.5);
+        R wt = sh ? R(w1[n + 11]) : R(w0[n + 11]);
+        R d = ax - t;
+        s += Math<R>::div_(wt, d * d + Y);
+    }
+    R re = R(0.5 * kInvPi) * y * s;       // (h / pi) y sum e^{-t^2} / ((x-t)^2 + y^2)
+    if (y < R(2)) {
+        // Re[ 2 e^{-z^2} / (1 -/+ e^{-2 pi i z / h}) ], h = 1/2: eta = 4 pi y, theta = 4 pi x
+        R em = Math<R>::expm1_(R(4 * kPI) * y);  // e^eta - 1
+        R E = R(1) + em;
+        R sn, cs;
+        Math<R>::sincospi_(R(4) * ax, &sn, &cs);
+        if (sh) {                          // theta + pi for the shifted lattice
+            sn = -sn;
+            cs = -cs;
+        }
+        R s2, c2;
+        Math<R>::sincos_(R(2) * ax * y, &s2, &c2);
+        R num = c2 * (R(1) - E * cs) - s2 * E * sn;
+        R den = em * em + R(2) * E * (R(1) - cs);
+        re += R(2) * Math<R>::exp_(Y - ax * ax) * num / den;
+    }
+    return re;
+}
+
+// Re w for any band; `X` = x^2, `Y` = y^2.
+template <typename R> __device__ __forceinline__ R voigt_re(R x, R y)
+{
+    R X = x * x, Y = y * y, r2 = X + Y;
+    const R k = R(kInvSqrtPi);
+    if (r2 >= BandLimits<R>::gh3) {
+        if (r2 >= BandLimits<R>::gh2)
+            return k * y * gh1_F<R>(r2);
+        return k * y * gh2_F<R>(X, Y, r2);
+    }
+    if (r2 >= BandLimits<R>::gh4)
+        return k * y * gh3_F<R>(X, Y, r2);
+    if (r2 >= BandLimits<R>::core)
+        return k * y * gh4_F<R>(X, Y, r2);
+    return core_re<R>(x, y);
+}
+
+// ---- problem descriptors ----------------------------------------------------
+
+// One sigma array to compute: one species at one (T, P), scalars prepared on
+// the host in FP64.
+struct Prob {
+    // line fields (device)
+    const double *nu0;
+    const float *S_ref, *A, *g_up, *E_low, *gamma, *n_T;
+    const double *S_pre;        // precomputed mode: S, alphaD_inv, y
+    const float *aDinv_pre, *y_pre;
+    int64_t n;
+    int s_mode;                 // 0 S_ref scaling, 1 Einstein A
+    int pre;                    // precomputed-parameter mode
+    // strength
+    double K2;                  // log2 Boltzmann slope: S-mode -c2(1/T - 1/T_ref)/ln2, A-mode -c2/(T ln2)
+    double qratio;              // S-mode Q(T_ref)/Q(T); A-mode 1/(8 pi c Q(T))
+    double c2T, c2Tref;         // c2/T, c2/T_ref
+    double mass_scale;          // 1/m[g] with HK_PER_GRAM, else 1
+    // widths
+    double aD_coef;             // alphaD_inv = aD_coef / nu0, aD_coef = c sqrt(m / (2 k_B T))
+    double log2_tratio;         // log2(T_ref / T)
+    double press;               // P / P_ref
+    double inv_Pref;            // 1 / P_ref
+    double nat_coef;            // 1 / (4 pi c)
+    // outputs
+    double *acc;                // [nbins] FP64 accumulator (or the FP64 output itself)
+    int *scale_exp;             // device int: sigma in acc is scaled by 2^-scale (FP32C)
+    unsigned *status;           // device status word (HK_STATUS_* bits)
+};
+
+// Bits of the per-device status word.
+constexpr unsigned kStatusRange = 1u;    // a float output overflowed
+constexpr unsigned kStatusTimeout = 2u;  // a bounded device wait gave up
+
+struct GridD {
+    double nu_min, dnu, inv_dnu;
+    double W;                   // cut / dnu (as cut * inv_dnu); <= 0: no cut
+    double cut;
+    int64_t nbins;
+};
+
+// Per-line kernel parameters, as staged in shared memory.
+struct LineP {
+    float b;     // dnu * alphaD^-1 (x step per bin)
+    float r;     // centre offset from bin i0 in bins, in [-1/2, 1/2] (see nearest_bin)
+    float y;     // Gamma_L * alphaD^-1
+    float s;     // S * alphaD^-1 / sqrt(pi) * 2^-scale  (FP32C)
+    int i0;      // nearest bin to the centre
+    int lo, hi;  // inclusive bin range inside the cut and the grid; empty if lo > hi
+    int pad;
+};
+
+// Cut predicate of the FP64 reading: |k - r| <= W (no FMA contraction).
+__device__ __forceinline__ bool in_cut(long long k, double r, double W)
+{
+    return fabs(__dsub_rn((double)k, r)) <= W;
+}
+
+// Bin geometry of one line.  Returns false if no bin of the grid is inside.
+__device__ __forceinline__ bool line_geometry(double nu0, const GridD &g, int *i0_out,
+                                              double *r_out, int *lo_out, int *hi_out)
+{
+    double u = __dmul_rn(__dsub_rn(nu0, g.nu_min), g.inv_dnu);
+    double f = floor(u);
+    double r = __dsub_rn(u, f);
+    long long i0 = (long long)f;
+    long long lo, hi;
+    if (g.W <= 0.0) {
+        lo = 0;
+        hi = g.nbins - 1;
+    } else {
+        long long kh = (long long)floor(__dadd_rn(r, g.W));
+        long long kl = (long long)ceil(__dsub_rn(r, g.W));
+        // walk to the exact predicate boundary (at most a step or two)
+        for (int it = 0; it < 4 && in_cut(kh + 1, r, g.W); ++it) ++kh;
+        for (int it = 0; it < 4 && !in_cut(kh, r, g.W) && kh >= kl; ++it) --kh;
+        for (int it = 0; it < 4 && in_cut(kl - 1, r, g.W); ++it) --kl;
+        for (int it = 0; it < 4 && !in_cut(kl, r, g.W) && kl <= kh; ++it) ++kl;
+        lo = i0 + kl;
+        hi = i0 + kh;
+        if (lo < 0) lo = 0;
+        if (hi > g.nbins - 1) hi = g.nbins - 1;
+    }
+    *r_out = r;
+    if (!(nu0 > 0.0)) hi = lo - 1;  // no Doppler width for nu0 <= 0 (Eq. gammaD): ignored
+    if (hi < lo || f < -2147483647.0 || f > 2147483647.0) {
+        // empty: a range no bin index can fall into, so every range test fails
+        *i0_out = 0;
+        *lo_out = 0x3fffffff;
+        *hi_out = -0x3fffffff;
+        return hi >= lo;  // an in-range line with an int32-overflowing centre cannot occur
+    }
+    *i0_out = (int)i0;
+    *lo_out = (int)lo;
+    *hi_out = (int)hi;
+    return true;
+}
+
+// Offset of bin i from the line centre in bins, as (i - c) - rn with the
+// NEAREST bin c and rn in [-1/2, 1/2]: for |i - c| >= 1 the float subtraction
+// is well conditioned and for i = c the offset is -rn itself, so a bin that
+// lies a tiny fraction of a bin from the centre keeps full relative
+// precision.  (i0, r) are the floor-based values of line_geometry.
+__device__ __forceinline__ void nearest_bin(int i0, double r, int *c, double *rn)
+{
+    if (r >= 0.5) {
+        *c = i0 + 1;
+        *rn = r - 1.0;
+    } else {
+        *c = i0;
+        *rn = r;
+    }
+}
+
+// Strength of line l in FP32 as a mantissa part P and a power of two: S *
+// alphaD_inv / sqrt(pi) * mass_scale = P * 2^e2.  Also returns alphaD_inv and y.
+__device__ __forceinline__ void line_strength_f32(const Prob &p, int64_t l, float *P_out,
+                                                  int *e2_out, float *aDinv_out, float *y_out)
+{
+    double nu0 = p.nu0[l];
+    float nu0f = (float)nu0;
+    float aDinv = (float)p.aD_coef / nu0f;
+    float nat = p.A ? p.A[l] * (float)p.nat_coef : 0.0f;
+    float GL = nat + p.gamma[l] * exp2f(p.n_T[l] * (float)p.log2_tratio) * (float)p.press;
+    double L = (double)p.E_low[l] * p.K2;   // log2 of the Boltzmann factor
+    double nL = rint(L);
+    float bz = exp2f((float)(L - nL));
+    float P;
+    if (p.s_mode == 0) {
+        float stim = expm1f(-(float)p.c2T * nu0f) / expm1f(-(float)p.c2Tref * nu0f);
+        P = p.S_ref[l] * (float)p.qratio * bz * stim;
+    } else {
+        float stim = -expm1f(-(float)p.c2T * nu0f);
+        P = p.A[l] * p.g_up[l] * (float)p.qratio / (nu0f * nu0f) * bz * stim;
+    }
+    P = P * (aDinv * (float)kInvSqrtPi) * (float)p.mass_scale;
+    *P_out = P;
+    *e2_out = (int)nL;
+    *aDinv_out = aDinv;
+    *y_out = GL * aDinv;
+}
+
+// FP64 strength S (no alphaD factor), alphaD_inv and y in double.
+__device__ __forceinline__ void line_strength_f64(const Prob &p, int64_t l, double *S_out,
+                                                  double *aDinv_out, double *y_out)
+{
+    double nu0 = p.nu0[l];
+    double aDinv = p.aD_coef / nu0;
+    double nat = p.A ? (double)p.A[l] * p.nat_coef : 0.0;
+    double GL = nat + (double)p.gamma[l] * exp2((double)p.n_T[l] * p.log2_tratio) * p.press;
+    double bz = exp2((double)p.E_low[l] * p.K2);
+    double S;
+    if (p.s_mode == 0) {
+        double stim = expm1(-p.c2T * nu0) / expm1(-p.c2Tref * nu0);
+        S = (double)p.S_ref[l] * p.qratio * bz * stim;
+    } else {
+        double stim = -expm1(-p.c2T * nu0);
+        S = (double)p.A[l] * (double)p.g_up[l] * p.qratio / (nu0 * nu0) * bz * stim;
+    }
+    *S_out = S * p.mass_scale;
+    *aDinv_out = aDinv;
+    *y_out = GL * aDinv;
+}
+
+// Two-sum: s + e = a + b exactly (Knuth).
+__device__ __forceinline__ void two_sum(float a, float b, float *s, float *e)
+{
+    float t = a + b;
+    float bp = t - a;
+    float ap = t - bp;
+    *e = (a - ap) + (b - bp);
+    *s = t;
+}
+
+}  // namespace hk

@@ -1,0 +1,48 @@
+// hk_launch.h -- host-side interfaces between the libhk translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/hk.h"
+#include "hk_internal.cuh"
+
+namespace hk {
+
+// Records a CUDA error for hk_last_cuda_error() and returns HK_ECUDA.
+int fail_cuda(cudaError_t e);
+
+// Gather (hk_gather.cu).  Tile width in bins for a precision / bins-per-thread.
+int gather_tile_bins(int precision, int bpt);
+// Workspace bytes of gather_run for nprob sigma arrays of nbins bins.
+size_t gather_workspace(int nprob, int64_t nbins, int precision, int bpt);
+// Runs the Voigt sum for nprob problems.  precision 0: FP32C, out is
+// float[nprob][nbins]; precision 1: FP64, out is double[nprob][nbins].
+// accumulate: add into out instead of overwriting.  probs_h is modified
+// (device pointers of the workspace are filled in).
+// out_f64: with precision 0, write double instead of float.  status_d: the
+// device status word (overflow of a float output is flagged there).
+int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt, int lmax,
+               void *out, int out_f64, int accumulate, char *ws, size_t ws_bytes,
+               unsigned *status_d, cudaStream_t st, int num_sms);
+
+// The per-device status word (allocated on first use).  Returns nullptr on failure.
+unsigned *status_word();
+
+// Profiling of the gather launches (hk_profile).
+void gather_profile_record(cudaStream_t st, bool begin);
+int gather_profile(int mode, double *ms, int64_t *launches);
+// Pair and band counts (hk_count_pairs).
+int count_pairs_run(const Prob &p, const GridD &g, unsigned long long *counts_d, cudaStream_t st,
+                    int num_sms);
+
+// Adjoint (hk_backward.cu).
+size_t backward_workspace(int64_t n, int nTP, int64_t nbins);
+int backward_run(Prob *probs_h, int nTP, const GridD &g, const float *grad_sigma,
+                 const double *dlnQ_dT, const double *T, const double *P, double *dL_dT,
+                 double *dL_dP, double *dL_dSref, double *dL_dgamma, const int64_t *perm,
+                 char *ws, size_t ws_bytes, cudaStream_t st, int num_sms);
+
+}  // namespace hk

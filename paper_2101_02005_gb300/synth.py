@@ -57,12 +57,16 @@ def lognormal_window_counts(n: int, nwin: int, seed: int, sigma: float = 1.5) ->
     return base
 
 
-def _sorted_uniform(rng: np.random.Generator, k: int, lo: float, hi: float) -> np.ndarray:
+def _sorted_uniform_into(rng: np.random.Generator, out: np.ndarray, lo: float, hi: float):
+    """Sorted U[lo, hi) sample of size out.size via normalised partial sums of
+    k + 1 exponential spacings (Renyi's representation of order statistics)."""
+    k = out.size
     if k == 0:
-        return np.zeros(0)
+        return
     e = rng.standard_exponential(k + 1)
-    c = np.cumsum(e)
-    return lo + (hi - lo) * (c[:k] / c[k])
+    np.cumsum(e, out=e)
+    np.multiply(e[:k], (hi - lo) / e[k], out=out)
+    out += lo
 
 
 @dataclass
@@ -119,18 +123,37 @@ def make_lines(n: int, nu_lo: float, nu_hi: float, seed: int, mass_amu: float,
     pos = 0
     for w, k in enumerate(counts.tolist()):
         if sort:
-            nu0[pos:pos + k] = _sorted_uniform(r_nu, k, edges[w], edges[w + 1])
+            _sorted_uniform_into(r_nu, nu0[pos:pos + k], edges[w], edges[w + 1])
         else:
-            nu0[pos:pos + k] = r_nu.uniform(edges[w], edges[w + 1], size=k)
+            r_nu.random(out=nu0[pos:pos + k])
+            nu0[pos:pos + k] *= edges[w + 1] - edges[w]
+            nu0[pos:pos + k] += edges[w]
         pos += k
-    lS0, lS1 = np.log10(S_range[0]), np.log10(S_range[1])
-    S_ref = np.power(10.0, stream(seed, "S_ref").uniform(lS0, lS1, size=n)).astype(np.float32)
-    E_low = stream(seed, "E_low").exponential(E_mean, size=n).astype(np.float32)
-    gamma = stream(seed, "gamma_ref").uniform(*gamma_range, size=n).astype(np.float32)
-    n_T = stream(seed, "n_T").uniform(*nT_range, size=n).astype(np.float32)
+    f32 = np.float32
+    # S_ref = 10^U[log10 S0, log10 S1], drawn in float32 in place
+    S_ref = np.empty(n, f32)
+    stream(seed, "S_ref").random(dtype=f32, out=S_ref)
+    l0, l1 = np.log(S_range[0]), np.log(S_range[1])
+    S_ref *= f32(l1 - l0)
+    S_ref += f32(l0)
+    np.exp(S_ref, out=S_ref)
+    E_low = np.empty(n, f32)
+    stream(seed, "E_low").standard_exponential(dtype=f32, out=E_low)
+    E_low *= f32(E_mean)
+    gamma = np.empty(n, f32)
+    stream(seed, "gamma_ref").random(dtype=f32, out=gamma)
+    gamma *= f32(gamma_range[1] - gamma_range[0])
+    gamma += f32(gamma_range[0])
+    n_T = np.empty(n, f32)
+    stream(seed, "n_T").random(dtype=f32, out=n_T)
+    n_T *= f32(nT_range[1] - nT_range[0])
+    n_T += f32(nT_range[0])
     A = None
     if A_range is not None:
-        A = stream(seed, "A").uniform(*A_range, size=n).astype(np.float32)
+        A = np.empty(n, f32)
+        stream(seed, "A").random(dtype=f32, out=A)
+        A *= f32(A_range[1] - A_range[0])
+        A += f32(A_range[0])
     return LineList(nu0, S_ref, E_low, gamma, n_T, float(mass_amu), A=A, sorted=bool(sort))
 
 

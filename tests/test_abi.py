@@ -1,0 +1,78 @@
+"""The C-ABI library loads and exports every entry point of include/hk.h;
+host-side argument checks and constants need no GPU."""
+import ctypes
+import json
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hk():
+    from paper_2101_02005_gb300 import build
+    build.build()
+    from paper_2101_02005_gb300 import hk
+    hk.lib()
+    return hk
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "hk.h")).read()
+    return sorted(set(re.findall(r"^(?:int|const char \*)\s*(hk_\w+)\(", src, re.M)))
+
+
+def test_every_declared_symbol_is_exported(hk):
+    names = declared_symbols()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(hk.lib(), n), n
+        assert n in hk.EXPORTS, n
+
+
+def test_constants_match_paper_and_oracle(hk):
+    import oracle
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
+    d = hk.hk_constants()
+    assert d["k_B"] == g["k_B"]["value"] and d["c"] == g["c"]["value"]
+    o = oracle.constants()
+    for k in d:
+        assert d[k] == o[k], k
+
+
+def test_strerror_and_version(hk):
+    L = hk.lib()
+    assert L.hk_strerror(0) == b"ok" and b"invalid" in L.hk_strerror(1)
+    assert L.hk_version() >= 100
+
+
+def test_invalid_arguments_rejected_on_host(hk):
+    L = hk.lib()
+    lines = hk.hk_lines(1, 2, None, None, 3, 4, 5, 10, 18.0, 0, 1)
+    grid = hk.make_grid(0.0, 0.1, 100)
+    st = hk.make_state(1000.0, 1.0, 3000.0)
+    op = hk.make_opts(500.0, 25.0)
+    b = ctypes.byref
+    assert L.hk_cross_section(None, b(grid), b(st), b(op), 1, None) == hk.HK_EINVAL
+    bad = hk.make_grid(0.0, -0.1, 100)
+    assert L.hk_cross_section(b(lines), b(bad), b(st), b(op), 1, None) == hk.HK_EINVAL
+    bad = hk.make_grid(0.0, 0.1, 0)
+    assert L.hk_cross_section(b(lines), b(bad), b(st), b(op), 1, None) == hk.HK_EINVAL
+    bst = hk.make_state(-1.0, 1.0, 3000.0)
+    assert L.hk_cross_section(b(lines), b(grid), b(bst), b(op), 1, None) == hk.HK_EINVAL
+    bst = hk.make_state(1000.0, -1.0, 3000.0)
+    assert L.hk_cross_section(b(lines), b(grid), b(bst), b(op), 1, None) == hk.HK_EINVAL
+    bop = hk.make_opts(500.0, float("nan"))
+    assert L.hk_cross_section(b(lines), b(grid), b(st), b(bop), 1, None) == hk.HK_EINVAL
+    bop = hk.make_opts(500.0, 25.0, precision=7)
+    assert L.hk_cross_section(b(lines), b(grid), b(st), b(bop), 1, None) == hk.HK_EINVAL
+    nl = hk.hk_lines(1, 2, None, None, 3, 4, 5, -1, 18.0, 0, 1)
+    assert L.hk_cross_section(b(nl), b(grid), b(st), b(op), 1, None) == hk.HK_EINVAL
+    nm = hk.hk_lines(1, None, None, None, 3, 4, 5, 10, 18.0, 0, 1)  # S-mode without S_ref
+    assert L.hk_cross_section(b(nm), b(grid), b(st), b(op), 1, None) == hk.HK_EINVAL
+    assert L.hk_cross_section(b(lines), b(grid), b(st), b(op), None, None) == hk.HK_EINVAL
+    out = ctypes.c_size_t(0)
+    assert L.hk_workspace_size(2, b(lines), 1, 1, b(grid), b(op), b(out)) == hk.HK_EINVAL
+    assert L.hk_constants(None) == hk.HK_EINVAL

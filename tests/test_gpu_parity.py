@@ -1,0 +1,248 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Bar: relative L1 <= 1e-5 and per-bin relative error <= 1e-4 over bins with
+sigma > 1e-10 max(sigma) (benchmark tolerance), for both the FP32-compensated
+and the FP64 GPU forms.  Inputs are the seeded synthetic workloads; sizes are
+chosen so the oracle finishes in seconds while spanning many tiles and a
+ragged tail.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from parity import assert_sigma_close, oracle_sigma_max, sigma_errors
+from paper_2101_02005_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+Q = synth.partition_function
+QREF = float(Q(296.0))
+
+
+@pytest.fixture(scope="module")
+def hk():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2101_02005_gb300 import build
+    build.build()
+    from paper_2101_02005_gb300 import hk
+    hk.lib()
+    return hk
+
+
+def oracle_sigma(L, grid, T, P, cut, bin_lo=0, bin_hi=None, per_gram=False):
+    return oracle.cross_section(L.as_oracle(), grid.astuple(), (T, P, float(Q(T)), QREF), cut,
+                                bin_lo, bin_hi, per_gram=per_gram)
+
+
+def gpu_sigma(hk, L, grid, T, P, cut, precision, flags=0):
+    D = hk.DeviceLines.from_host(L)
+    s = hk.hk_cross_section(D, hk.make_grid(*grid.astuple()),
+                            hk.make_state(T, P, float(Q(T)), float(synth.dlnQ_dT(T))),
+                            hk.make_opts(QREF, cut, precision, flags=flags))
+    hk.hk_sync_status()
+    return s.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_config0_full(hk, prec):
+    w = synth.config(0)
+    L = w.species[0]
+    T, P = w.states()[0]
+    ref = oracle_sigma(L, w.grid, T, P, w.cut)
+    got = gpu_sigma(hk, L, w.grid, T, P, w.cut, prec)
+    e = assert_sigma_close(got, ref, f"c0 prec={prec}")
+    # at 1000 K a few high-E'' lines dominate max(sigma); a few % of bins pass the mask
+    assert e["n_mask"] > 500
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ragged_grid_off_grid_lines_and_cut_variants(hk, prec):
+    rng = np.random.default_rng(17)
+    n = 700
+    nu0 = np.sort(np.concatenate([rng.uniform(-3.0, 103.0, n - 4), [-2.5, 0.0, 99.95, 102.7]]))
+    L = synth.LineList(nu0, (10 ** rng.uniform(-24, -20, n)).astype(np.float32),
+                       rng.exponential(2000, n).astype(np.float32),
+                       rng.uniform(0.01, 0.1, n).astype(np.float32),
+                       rng.uniform(0.3, 0.8, n).astype(np.float32), 18.0)
+    for nbins, cut in [(1037, 2.5), (2048 + 513, 0.05), (1000, 0.0), (333, 500.0)]:
+        grid = synth.Grid(0.0, 100.0 / nbins, nbins)
+        ref = oracle_sigma(L, grid, 700.0, 0.3, cut)
+        got = gpu_sigma(hk, L, grid, 700.0, 0.3, cut, prec)
+        assert_sigma_close(got, ref, f"nbins={nbins} cut={cut} prec={prec}")
+        # bins outside every line's cut are exactly zero on both sides
+        assert np.array_equal(ref == 0, got == 0)
+
+
+def test_zero_lines_and_single_line(hk):
+    L0 = synth.make_lines(0, 0, 10, 1, 18.0)
+    grid = synth.Grid(0.0, 0.01, 1000)
+    got = gpu_sigma(hk, L0, grid, 500.0, 1.0, 1.0, 0)
+    assert np.all(got == 0)
+    L1 = synth.make_lines(1, 4.0, 6.0, 2, 18.0)
+    ref = oracle_sigma(L1, grid, 500.0, 1.0, 1.0)
+    for prec in (0, 1):
+        assert_sigma_close(gpu_sigma(hk, L1, grid, 500.0, 1.0, 1.0, prec), ref, f"1 line {prec}")
+
+
+def test_unsorted_input_matches_oracle(hk):
+    L = synth.make_lines(3000, 0.0, 300.0, 5, 18.0, sort=False)
+    grid = synth.Grid(0.0, 0.05, 6000)
+    ref = oracle_sigma(L, grid, 1200.0, 2.0, 5.0)
+    assert_sigma_close(gpu_sigma(hk, L, grid, 1200.0, 2.0, 5.0, 0), ref, "unsorted")
+
+
+def test_einstein_A_mode_per_gram(hk):
+    rng = np.random.default_rng(3)
+    L = synth.make_lines(2000, 100.0, 400.0, 9, 56.0, A_range=(1e6, 1e9))
+    L.g_up = rng.integers(1, 20, L.n).astype(np.float32)
+    L.s_mode = 1
+    grid = synth.Grid(100.0, 0.02, 15000)
+    ref = oracle_sigma(L, grid, 2500.0, 0.1, 10.0, per_gram=True)
+    for prec in (0, 1):
+        got = gpu_sigma(hk, L, grid, 2500.0, 0.1, 10.0, prec, flags=1)
+        assert_sigma_close(got, ref, f"A-mode prec={prec}")
+
+
+def test_float_overflow_reports_erange_and_double_output_is_exact(hk):
+    """One line of large E'' at high T: S(T) ~ 1e56, sigma beyond the float
+    range.  Float output must be reported (HK_ERANGE), double output must match."""
+    L = synth.make_lines(3, 10.0, 20.0, 8, 18.0)
+    L.E_low[:] = np.float32(60000.0)
+    L.S_ref[:] = np.float32(1e-19)
+    grid = synth.Grid(0.0, 0.01, 3000)
+    T, P, cut = 2500.0, 1.0, 5.0
+    D = hk.DeviceLines.from_host(L)
+    args = (hk.make_grid(*grid.astuple()), hk.make_state(T, P, float(Q(T))))
+    hk.hk_sync_status()
+    hk.hk_cross_section(D, *args, hk.make_opts(QREF, cut))
+    with pytest.raises(hk.HKError) as ei:
+        hk.hk_sync_status()
+    assert ei.value.status == hk.HK_ERANGE
+    hk.hk_sync_status()                                  # the status word was cleared
+    s = hk.hk_cross_section(D, *args, hk.make_opts(QREF, cut, flags=hk.HK_SIGMA_F64))
+    hk.hk_sync_status()
+    ref = oracle_sigma(L, grid, T, P, cut)
+    assert ref.max() > 1e45
+    assert_sigma_close(s.cpu().numpy(), ref, "double output of FP32C")
+
+
+def test_line_strength_and_widths(hk):
+    L = synth.config(0).species[0]
+    D = hk.DeviceLines.from_host(L)
+    T, P = 1777.0, 0.37
+    st = hk.make_state(T, P, float(Q(T)))
+    op = hk.make_opts(QREF, 25.0)
+    S = hk.hk_line_strength(D, st, op).cpu().numpy()
+    aDinv, y = (t.cpu().numpy() for t in hk.hk_widths(D, st, op))
+    So = oracle.line_strength(L.nu0, L.E_low, T, float(Q(T)), QREF, 18.0, S_ref=L.S_ref)
+    aD, GL = oracle.widths(L.nu0, L.gamma_ref, L.n_T, T, P, 18.0)
+    m = So > 1e-300
+    assert np.allclose(S[m], So[m], rtol=1e-11, atol=0)
+    assert np.allclose(aDinv, 1 / aD, rtol=2e-7)
+    assert np.allclose(y, GL / aD, rtol=2e-7)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_voigt_accumulate_adds(hk, prec):
+    L = synth.make_lines(1500, 0.0, 150.0, 21, 18.0)
+    grid = synth.Grid(0.0, 0.01, 15000)
+    T, P, cut = 900.0, 0.5, 3.0
+    S = oracle.line_strength(L.nu0, L.E_low, T, float(Q(T)), QREF, 18.0, S_ref=L.S_ref)
+    aD, GL = oracle.widths(L.nu0, L.gamma_ref, L.n_T, T, P, 18.0)
+    ref = oracle.sigma(L.nu0, S, aD, GL, *grid.astuple(), cut)
+    dt = torch.float64 if prec else torch.float32
+    # a non-zero starting sigma of the same magnitude (so the float difference
+    # after - before is well conditioned)
+    start_np = 0.37 * ref
+    start_np[::7] = 0.0
+    base = torch.from_numpy(start_np).to(dt).cuda()
+    start = base.clone()
+    hk.hk_voigt_accumulate(torch.from_numpy(L.nu0).cuda(), torch.from_numpy(S).cuda(),
+                           torch.from_numpy((1 / aD).astype(np.float32)).cuda(),
+                           torch.from_numpy((GL / aD).astype(np.float32)).cuda(),
+                           hk.make_grid(*grid.astuple()), cut, base, prec)
+    hk.hk_sync_status()
+    got = (base - start).cpu().numpy().astype(np.float64)
+    assert_sigma_close(got, ref, "voigt_accumulate")
+
+
+def test_config1_shape_windows(hk):
+    """Config 1 shape (log-normal density, 0.1 grid, cut 25, 1500 K) at 1/100 of
+    its line count: whole array on the GPU, windows (dense, sparse, edges) on
+    the oracle."""
+    w = synth.config(1, scale=1e-2)
+    L = w.species[0]
+    T, P = w.states()[0]
+    D = hk.DeviceLines.from_host(L)
+    # at 1500 K lines of large E'' reach S(T) ~ 1e40: sigma needs double output
+    got = hk.hk_cross_section(D, hk.make_grid(*w.grid.astuple()),
+                              hk.make_state(T, P, float(Q(T))),
+                              hk.make_opts(QREF, w.cut, flags=hk.HK_SIGMA_F64))
+    hk.hk_sync_status()
+    got = got.cpu().numpy().astype(np.float64)
+    counts = synth.lognormal_window_counts(L.n, 300, synth.SEED_BASE + 1)
+    dense = int(np.argmax(counts))
+    sparse = int(np.argmin(counts))
+    gmax = oracle_sigma_max(oracle, L, w.grid.astuple(), (T, P, float(Q(T)), QREF), w.cut)
+    assert gmax <= got.max() * (1 + 1e-4)
+    for lo in [0, dense * 1000 + 300, sparse * 1000 + 300, w.grid.nbins - 1500]:
+        hi = lo + 1500
+        ref = oracle_sigma(L, w.grid, T, P, w.cut, lo, hi)
+        assert_sigma_close(got[lo:hi], ref, f"c1/100 window {lo}", ref_max=gmax)
+
+
+def test_batched_matches_single(hk):
+    """Config 3 shape at reduced line counts; every (species, T, P) array of the
+    batched launch against the oracle on two windows."""
+    w = synth.config(3, scale=2e-4)
+    grid = synth.Grid(0.0, 0.01, 200000)          # 0-2000 cm^-1 slice of the grid
+    species = [hk.DeviceLines.from_host(s) for s in w.species]
+    Ts = w.T[::6]
+    Ps = w.P[::3]
+    states = [hk.make_state(t, p, float(Q(t))) for t in Ts for p in Ps]
+    out = hk.hk_cross_section_batched(species, states, hk.make_grid(*grid.astuple()),
+                                      hk.make_opts(QREF, w.cut, flags=hk.HK_SIGMA_F64))
+    hk.hk_sync_status()
+    out = out.cpu().numpy()
+    k = 0
+    for t in Ts:
+        for p in Ps:
+            for s, L in enumerate(w.species):
+                gmax = oracle_sigma_max(oracle, L, grid.astuple(), (t, p, float(Q(t)), QREF), w.cut)
+                for lo in (1000, 150000):
+                    ref = oracle_sigma(L, grid, t, p, w.cut, lo, lo + 400)
+                    assert_sigma_close(out[s, k, lo:lo + 400], ref,
+                                       f"batched s={s} T={t:.0f} P={p:.1e}", ref_max=gmax)
+            k += 1
+
+
+def test_backward_matches_oracle_gradient(hk):
+    """Config 4 shape (cut 25, 0.01 grid, paired T-P points) at reduced size."""
+    rng = np.random.default_rng(44)
+    L = synth.make_lines(300, 0.0, 100.0, synth.SEED_BASE + 4, 18.0)
+    grid = synth.Grid(0.0, 0.01, 10000)
+    Ts = np.array([300.0, 800.0, 2500.0])
+    Ps = np.array([1e-3, 0.3, 10.0])
+    cut = 25.0
+    g = rng.standard_normal((3, grid.nbins)).astype(np.float32)
+    D = hk.DeviceLines.from_host(L)
+    states = [hk.make_state(t, p, float(Q(t)), float(synth.dlnQ_dT(t))) for t, p in zip(Ts, Ps)]
+    dT, dP, dS, dG = hk.hk_cross_section_backward(D, hk.make_grid(*grid.astuple()), states,
+                                                  hk.make_opts(QREF, cut),
+                                                  torch.from_numpy(g).cuda())
+    hk.hk_sync_status()
+    dT, dP, dS, dG = (x.cpu().numpy() for x in (dT, dP, dS, dG))
+    oS = np.zeros(L.n)
+    oG = np.zeros(L.n)
+    for k, (t, p) in enumerate(zip(Ts, Ps)):
+        _, _, oT, oP = oracle.backward(L.as_oracle(), grid.astuple(),
+                                       (t, p, float(Q(t)), QREF, float(synth.dlnQ_dT(t))), cut,
+                                       g[k].astype(np.float64), oS, oG)
+        assert abs(dT[k] - oT) <= 1e-4 * abs(oT), (k, dT[k], oT)
+        assert abs(dP[k] - oP) <= 1e-4 * abs(oP), (k, dP[k], oP)
+    assert np.linalg.norm(dS - oS) <= 1e-4 * np.linalg.norm(oS)
+    assert np.linalg.norm(dG - oG) <= 1e-4 * np.linalg.norm(oG)

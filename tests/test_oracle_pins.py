@@ -201,6 +201,9 @@ def test_cut_ranges_vs_exact_rationals():
     def check(nu0, exact):
         lo, hi = oracle.line_ranges(nu0, nu_min, dnu, nbins, cut)
         for l in range(nu0.size):
+            if nu0[l] <= 0:              # reading: no Doppler width, the line adds nothing
+                assert hi[l] < lo[l]
+                continue
             v = exact(nu0[l])
             c = int(nu0[l] / dnu)
             inside = [i for i in range(max(0, c - 40), min(nbins, c + 40))
