@@ -1,0 +1,399 @@
+"""Throughput of the HELIOS-K opacity hot path on GB300.
+
+One step = one hk_cross_section call over the whole line list at one (T, P):
+line strengths, widths, bin geometry, the Voigt sum and the final write
+(every step of the path).  Default workload: the 5e8-line water-like list
+(log-normal line density over 0-30000 cm^-1), 0.1 cm^-1 grid (3e5 bins),
+25 cm^-1 cut, T = 1500 K, P = 1 bar, FP32-compensated arithmetic.
+
+Prints one JSON line.  value = lines/s over all ranks (device time, inputs
+resident in HBM); e2e = the same metric with the line list copied from
+pinned host memory and sigma copied back inside every timed step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "lines/s and Voigt evals/s on 1 GB300 (FP32-comp vs FP64 GPU) at stated σ error"
+
+# Cost model: FP32 flops per (line, bin) pair in each Faddeeva band of the
+# kernel (FMA = 2 flops; reciprocals, exp and sincos counted as 1 each):
+# shared x, x^2, r^2 and accumulate = 6; band formulas add 2 / 8 / 13 / 19
+# and ~194 for the trapezoid core.  Band counts come from hk_count_pairs.
+FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 19, "gh4": 25, "core": 200}
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--scale", type=float, default=1.0, help="line-count scale (1 = full)")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def workload(args):
+    from paper_2101_02005_gb300 import synth
+    w = synth.config(args.config, scale=args.scale)
+    return w
+
+
+def cpu_sample(w, L, T, P, seconds_target=15.0, nthreads=0):
+    """Times the FP64 oracle (as it stands) on windows of the grid, growing the
+    sample until it has taken ~seconds_target; returns pairs/s, the windows and
+    the oracle's sigma on them."""
+    import oracle
+    from paper_2101_02005_gb300 import synth
+    Q = synth.partition_function
+    grid = w.grid.astuple()
+    state = (T, P, float(Q(T)), float(Q(296.0)))
+    # windows at the median-density 100 cm^-1 window of the list
+    counts = synth.lognormal_window_counts(L.n, 300, synth.SEED_BASE + w_seed_offset(w)) \
+        if L.n >= 300 else None
+    if counts is not None and w.grid.nbins >= 3000:
+        med = int(np.argsort(counts)[len(counts) // 2])
+        start = med * (w.grid.nbins // 300) + 50
+    else:
+        start = w.grid.nbins // 2
+    width = 16
+    t_used = 0.0
+    pairs = 0
+    wins = []
+    while t_used < seconds_target and width <= 4096:
+        lo, hi = start, min(w.grid.nbins, start + width)
+        # pairs inside this window: lines whose cut range overlaps it
+        sel = np.searchsorted(L.nu0, [grid[0] + lo * grid[1] - w.cut - grid[1],
+                                      grid[0] + hi * grid[1] + w.cut + grid[1]])
+        sub = L.subset(slice(int(sel[0]), int(sel[1])))
+        rlo, rhi = oracle.line_ranges(sub.nu0, *grid, w.cut)
+        n_pairs = int(np.clip(np.minimum(rhi, hi - 1) - np.maximum(rlo, lo) + 1, 0, None).sum())
+        t0 = time.perf_counter()
+        ref = oracle.cross_section(sub.as_oracle(), grid, state, w.cut, lo, hi, nthreads=nthreads)
+        dt = time.perf_counter() - t0
+        t_used += dt
+        pairs += n_pairs
+        wins.append((lo, hi, ref, dt, n_pairs))
+        start = hi
+        width *= 2
+    return pairs / max(t_used, 1e-9), t_used, pairs, wins
+
+
+def w_seed_offset(w):
+    return 1 if w.name.startswith("c1") else (2 if w.name.startswith("c2") else 0)
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the host cores, same workload
+    and metric, each step a bounded window of the grid."""
+    import oracle  # noqa: F401
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args)
+    L = w.species[0]
+    T, P = w.states()[0]
+    import oracle as orc
+    total_pairs = orc.count_pairs(L.nu0, *w.grid.astuple(), w.cut)
+    pairs_per_line = total_pairs / L.n
+    cores = os.cpu_count()
+    rates = []
+    sample = ""
+    for s in range(args.warmup + args.steps):
+        rate, secs, pairs, wins = cpu_sample(w, L, T, P, seconds_target=4.0)
+        if s >= args.warmup:
+            rates.append(rate)
+        sample = (f"bins {wins[0][0]}-{wins[-1][1]} of the median-density window, "
+                  f"{pairs} pairs in {secs:.1f} s per step")
+    rate = statistics.median(rates)
+    value = rate / pairs_per_line
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "lines/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": L.n / value * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "lines": L.n, "bins": w.grid.nbins,
+                       "pairs": total_pairs},
+            "e2e": {"value": value, "unit": "lines/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "cpu_baseline": {"value": value, "unit": "lines/s", "cores": cores,
+                             "kind": "oracle", "sample": sample,
+                             "note": "extrapolated from pairs/s over the whole list"}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2101_02005_gb300 import build as pbuild
+    pbuild.build()
+    from paper_2101_02005_gb300 import hk, synth
+
+    t_gen = time.perf_counter()
+    w = workload(args)
+    L = w.species[0]
+    T, P = w.states()[0]
+    Q = synth.partition_function
+    t_gen = time.perf_counter() - t_gen
+
+    # line list resident in HBM; pinned host copies for the end-to-end timing
+    host = {k: torch.from_numpy(getattr(L, k)) for k in ("nu0", "S_ref", "E_low", "gamma_ref", "n_T")}
+    D = hk.DeviceLines(*(host[k].to(dev) for k in ("nu0", "S_ref", "E_low", "gamma_ref", "n_T")),
+                       L.mass_amu, s_mode=L.s_mode, sorted=L.sorted)
+    grid = hk.make_grid(*w.grid.astuple())
+    state = hk.make_state(T, P, float(Q(T)), float(synth.dlnQ_dT(T)))
+    opts = hk.make_opts(float(Q(296.0)), w.cut, hk.HK_FP32C, flags=hk.HK_SIGMA_F64)
+    sigma = torch.empty(w.grid.nbins, dtype=torch.float64, device=dev)
+    counts = hk.hk_count_pairs(D, grid, state, opts)
+    pairs = counts[0]
+    bands = dict(zip(["gh1", "gh2", "gh3", "gh4", "core"], counts[1:]))
+    flops_step = sum(FLOPS_PER_PAIR[b] * n for b, n in bands.items())
+    stream = torch.cuda.current_stream()
+
+    def step():
+        hk.hk_cross_section(D, grid, state, opts, sigma)
+
+    for _ in range(args.warmup):
+        step()
+    hk.hk_sync_status()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    barrier()
+    sampler.start()
+    time.sleep(0.3)
+    hk.hk_profile(1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    gather_ms, gather_launches = hk.hk_profile(0)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    hk.hk_sync_status()
+    ms_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    ms_step = ms_max / args.steps
+    value = world * L.n / (ms_step / 1e3)
+
+    # roofline of the dominant kernel (the Voigt gather), live CUDA-event time
+    peaks = load_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    g_ms = gather_ms / max(gather_launches, 1)
+    achieved = flops_step / (g_ms / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": "k_gather<float,4>", "achieved": achieved,
+                "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
+                "traffic": None, "gather_ms_per_launch": g_ms,
+                "gather_share_of_step": g_ms / ms_step if ms_step else None,
+                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+                              f"{sm_max:.0f} MHz (derived, FP32 FMA)",
+                "flops_per_step": flops_step, "cost_model": FLOPS_PER_PAIR}
+
+    # end to end: pinned host -> device copies of the lines, the call, sigma back
+    e2e = None
+    if not args.no_e2e:
+        pinned = {k: v.pin_memory() for k, v in host.items()}
+        out_h = torch.empty(w.grid.nbins, dtype=torch.float64).pin_memory()
+        dstt = {"nu0": D.nu0, "S_ref": D.S_ref, "E_low": D.E_low, "gamma_ref": D.gamma_ref,
+                "n_T": D.n_T}
+        h2d = sum(v.numel() * v.element_size() for v in pinned.values())
+        d2h = out_h.numel() * out_h.element_size()
+
+        def e2e_step():
+            for k, v in pinned.items():
+                dstt[k].copy_(v, non_blocking=True)
+            hk.hk_cross_section(D, grid, state, opts, sigma)
+            out_h.copy_(sigma, non_blocking=True)
+
+        e2e_step()
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        f1.record(stream)
+        barrier()
+        ems = f0.elapsed_time(f1)
+        if dist is not None:
+            t = torch.tensor([ems], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * L.n / (ems / args.steps / 1e3), "unit": "lines/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": ems / args.steps}
+        del pinned
+
+    # the plain FP64 GPU form on every 10th line (per-line work is the same
+    # for every line: the cut admits 2 cut/dnu + 1 bins whatever the density)
+    fp64 = None
+    if not args.no_fp64:
+        sub = slice(0, None, 10)
+        D64 = hk.DeviceLines(D.nu0[sub].contiguous(), D.S_ref[sub].contiguous(),
+                             D.E_low[sub].contiguous(), D.gamma_ref[sub].contiguous(),
+                             D.n_T[sub].contiguous(), L.mass_amu)
+        o64 = hk.make_opts(float(Q(296.0)), w.cut, hk.HK_FP64)
+        s64 = torch.empty(w.grid.nbins, dtype=torch.float64, device=dev)
+        hk.hk_cross_section(D64, grid, state, o64, s64)
+        torch.cuda.synchronize()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        hk.hk_cross_section(D64, grid, state, o64, s64)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        f64ms = g0.elapsed_time(g1)
+        c64 = hk.hk_count_pairs(D64, grid, state, o64)[0]
+        fp64 = {"value": D64.n / (f64ms / 1e3), "unit": "lines/s",
+                "voigt_evals_per_s": c64 / (f64ms / 1e3), "ms": f64ms,
+                "sample": "every 10th line of the list, one step"}
+        del D64, s64
+
+    # CPU baseline (oracle as it stands, host cores) on a bounded sample, which
+    # doubles as a parity check of this run's sigma on the same bins
+    cpu = None
+    parity = None
+    if not args.no_cpu and rank == 0:
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from parity import sigma_errors as sigma_errors_window
+        rate, secs, cpairs, wins = cpu_sample(w, L, T, P, seconds_target=15.0)
+        pairs_per_line = pairs / L.n
+        cpu = {"value": rate / pairs_per_line, "unit": "lines/s", "cores": os.cpu_count(),
+               "kind": "oracle", "voigt_evals_per_s": rate,
+               "sample": f"bins {wins[0][0]}-{wins[-1][1]} of the median-density 100 cm^-1 "
+                         f"window, {cpairs} pairs in {secs:.1f} s, extrapolated to the list"}
+        got = sigma.cpu().numpy()
+        errs = [sigma_errors_window(got[lo:hi], ref) for lo, hi, ref, _, _ in wins]
+        parity = {"rel_l1_max": max(e["l1"] for e in errs),
+                  "max_bin_rel": max(e["max_bin"] for e in errs),
+                  "bins": int(sum(hi - lo for lo, hi, _, _, _ in wins)),
+                  "note": "window-local mask (stricter than the array-wide one)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "lines/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "lines_per_gpu": L.n, "bins": w.grid.nbins,
+                           "voigt_pairs_per_step": pairs, "precision": "FP32-compensated",
+                           "sigma_out": "f64",
+                           "l2": "inputs (24 B/line, %.1f GB) larger than L2" % (24 * L.n / 1e9),
+                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                           "band_pairs": bands, "generation_s": round(t_gen, 1)},
+                "voigt_evals_per_s": world * pairs / (ms_step / 1e3),
+                "gpu_launches": 5 * args.steps,
+                "roofline": roofline, "clocks": clocks, "e2e": e2e, "fp64_gpu": fp64,
+                "cpu_baseline": cpu, "parity_sample": parity}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -472,7 +472,11 @@ int gather_profile(int mode, double *ms, int64_t *launches)
 
 // ---- host side ----------------------------------------------------------------
 
-int gather_tile_bins(int precision, int bpt) { return NWARPS * 32 * (precision == 1 ? 2 : bpt); }
+int gather_tile_bins(int precision, int bpt)
+{
+    (void)bpt;
+    return precision == 1 ? NWARPS * 32 * 2 : gather_f32_tile_bins();
+}
 
 size_t gather_workspace(int nprob, int64_t nbins, int precision, int bpt)
 {
@@ -551,11 +555,9 @@ int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt,
         dim3 grid(num_sms * 2);
         gather_profile_record(st, true);
         if (precision == 0) {
-            switch (bpt) {
-            case 2: k_gather<float, 2><<<grid, NTHREADS, 0, st>>>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter); break;
-            case 8: k_gather<float, 8><<<grid, NTHREADS, 0, st>>>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter); break;
-            default: k_gather<float, 4><<<grid, NTHREADS, 0, st>>>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter); break;
-            }
+            int rc = gather_f32_launch(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
+                                       counter, st, num_sms);
+            if (rc) return rc;
         } else {
             k_gather<double, 2><<<grid, NTHREADS, 0, st>>>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter);
         }

@@ -31,6 +31,13 @@ int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt,
 // The per-device status word (allocated on first use).  Returns nullptr on failure.
 unsigned *status_word();
 
+// FP32-compensated line-major gather (hk_gather_f32.cu).
+int gather_f32_tile_bins();
+size_t gather_f32_smem();
+int gather_f32_launch(const Prob *probs_d, const GridD &g, int64_t ntiles, int64_t m,
+                      const int64_t *item_off, const int64_t *tile_lb, const int64_t *tile_le,
+                      int lmax, unsigned long long *counter, cudaStream_t st, int num_sms);
+
 // Profiling of the gather launches (hk_profile).
 void gather_profile_record(cudaStream_t st, bool begin);
 int gather_profile(int mode, double *ms, int64_t *launches);
