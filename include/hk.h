@@ -67,6 +67,7 @@ extern "C" {
 #define HK_ENOTSUP 5  /* combination of options not supported */
 #define HK_ERANGE 6   /* a float sigma output overflowed (reported by hk_sync_status);
                          request double output with HK_SIGMA_F64 */
+#define HK_ESIZE 7    /* the grid is larger than hk_cross_section_noalloc's fixed scratch */
 
 /* ---- enums -------------------------------------------------------------- */
 /* line-strength mode (Sect. 2.2.2) */
@@ -173,6 +174,42 @@ int hk_voigt_accumulate(const double *nu0, const double *S, const float *alphaD_
  * Doppler width (Eq. gammaD) and contribute nothing. */
 int hk_cross_section(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
                      const hk_opts *opts, void *sigma_out, void *stream);
+
+/* hk_cross_section for callers that must not allocate device memory.  The
+ * paper has no counterpart; this is a service of the library.
+ *
+ * Some callers cannot let a library call cudaMalloc: an application that
+ * owns every byte of the GPU through its own allocator and forbids other
+ * allocations, a process with a hard device-memory budget, or a loop that
+ * cannot afford the device-wide synchronisation cudaMalloc/cudaFree imply.
+ * This entry point computes exactly what hk_cross_section computes (same
+ * kernels, same arithmetic, same output layout) but takes its scratch
+ * memory -- the FP64 accumulator, the per-tile line ranges and the work
+ * counter -- from one fixed array that the library declares in device
+ * memory: HK_NOALLOC_SCRATCH_BYTES (16 MiB).  Every GPU that loads libhk
+ * holds that array until the process exits; this call never calls cudaMalloc,
+ * cudaFree or any allocating routine.
+ *
+ * Limits: the lines must be sorted (hk_lines.sorted = 1; sorting needs
+ * scratch proportional to n, so unsorted lists return HK_ENOTSUP); the grid
+ * must fit the array: about 2.09e6 bins for HK_FP32C and 2.6e8 for HK_FP64,
+ * exactly when hk_cross_section's workspace plus 256 bytes is at most
+ * HK_NOALLOC_SCRATCH_BYTES; larger grids return HK_ESIZE before anything is
+ * enqueued.  A float output that overflows is not reported (its status flag
+ * lives in the array); request HK_SIGMA_F64 when S(T) can exceed the float
+ * range.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the one array,
+ * which keeps the previous call's contents (the call clears what must start
+ * at zero), so calls whose work overlaps on the GPU -- on different streams
+ * without ordering -- race and must be serialised by the caller.
+ * sigma_out: DEVICE float[nbins] (HK_FP32C) or double[nbins] (HK_FP64, or
+ * HK_SIGMA_F64), overwritten. */
+#define HK_NOALLOC_SCRATCH_BYTES (16u << 20)
+int hk_cross_section_noalloc(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
+                             const hk_opts *opts, void *sigma_out, void *stream);
 
 /* Opacity table in one persistent launch: every species x every (T, P)
  * point (pressure batching of Sect. 2.4.6 / Sect. 3.5, generalised to a T-P

@@ -363,6 +363,7 @@ const char *hk_strerror(int s)
     case HK_ETIMEOUT: return "bounded device wait gave up";
     case HK_ENOTSUP: return "unsupported combination of options";
     case HK_ERANGE: return "a float sigma output overflowed (use HK_SIGMA_F64)";
+    case HK_ESIZE: return "grid too large for the fixed scratch of hk_cross_section_noalloc";
     default: return "unknown status";
     }
 }
@@ -540,6 +541,67 @@ int hk_cross_section(const hk_lines *lines, const hk_grid *grid, const hk_state 
     Tune t = get_tune(opts->precision);
     return cross_section_impl(lines, grid, state, opts, sigma_out, (cudaStream_t)stream, t.bpt,
                               t.lmax);
+}
+
+// ---- hk_cross_section_noalloc: scratch in a fixed device array ---------------
+// The array lives in device memory of every GPU that loads the library.  Host
+// code must never hand the symbol itself to a kernel (on the host it names a
+// host-side shadow); the device address comes from cudaGetSymbolAddress, looked
+// up once per device with that device current.  Layout: [0, 256) a status word
+// for the finalize kernel, [256, HK_NOALLOC_SCRATCH_BYTES) the gather's scratch.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HK_NOALLOC_SCRATCH_BYTES];
+static std::mutex g_noalloc_mu;
+static std::map<int, char *> g_noalloc_addr;
+
+static int noalloc_scratch(char **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return fail_cuda(e);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(dev);
+    if (it != g_noalloc_addr.end()) {
+        *out = it->second;
+        return HK_OK;
+    }
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return fail_cuda(e ? e : cudaErrorInvalidSymbol);
+    g_noalloc_addr[dev] = (char *)p;
+    *out = (char *)p;
+    return HK_OK;
+}
+
+int hk_cross_section_noalloc(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
+                             const hk_opts *opts, void *sigma_out, void *stream)
+{
+    int rc;
+    if ((rc = check_lines(lines, true)) || (rc = check_grid(grid)) || (rc = check_state(state)) ||
+        (rc = check_opts(opts)))
+        return rc;
+    if (!sigma_out) return HK_EINVAL;
+    if (lines->n > 0 && !lines->sorted) return HK_ENOTSUP;
+    const int prec = opts->precision;
+    Tune t = get_tune(prec);
+    const size_t need = gather_workspace(1, grid->nbins, prec, t.bpt);
+    if (need + 256 > (size_t)HK_NOALLOC_SCRATCH_BYTES) return HK_ESIZE;
+    char *scratch;
+    if ((rc = noalloc_scratch(&scratch))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int out_f64 = (opts->flags & HK_SIGMA_F64) ? 1 : 0;
+    cudaError_t e;
+    if (lines->n == 0) {
+        size_t b = (size_t)grid->nbins * ((prec == HK_FP64 || out_f64) ? 8 : 4);
+        e = cudaMemsetAsync(sigma_out, 0, b, st);
+        return e ? fail_cuda(e) : HK_OK;
+    }
+    unsigned *status = (unsigned *)scratch;
+    if ((e = cudaMemsetAsync(status, 0, sizeof(unsigned), st))) return fail_cuda(e);
+    GridD g = make_grid(grid, opts);
+    Prob p = make_prob(lines, state, opts);
+    // gather_run clears the accumulator, the scale slot and the work counter
+    return gather_run(&p, 1, g, prec, t.bpt, t.lmax, sigma_out, out_f64, 0, scratch + 256, need,
+                      status, st, num_sms());
 }
 
 int hk_workspace_size(int kind, const hk_lines *species, int nspecies, int nTP,

@@ -15,7 +15,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libhk.so")
 
-HK_OK, HK_EINVAL, HK_ENOMEM, HK_ECUDA, HK_ETIMEOUT, HK_ENOTSUP, HK_ERANGE = 0, 1, 2, 3, 4, 5, 6
+HK_OK, HK_EINVAL, HK_ENOMEM, HK_ECUDA, HK_ETIMEOUT, HK_ENOTSUP, HK_ERANGE, HK_ESIZE = range(8)
+HK_NOALLOC_SCRATCH_BYTES = 16 << 20
 HK_S_REF, HK_S_EINSTEIN_A = 0, 1
 HK_FP32C, HK_FP64 = 0, 1
 HK_CUT_FIXED, HK_CUT_NONE = 0, 1
@@ -25,7 +26,8 @@ HK_SIGMA_F64 = 2
 EXPORTS = ["hk_line_strength", "hk_widths", "hk_voigt_accumulate", "hk_cross_section",
            "hk_cross_section_batched", "hk_cross_section_backward", "hk_workspace_size",
            "hk_autotune", "hk_sync_status", "hk_release", "hk_strerror", "hk_last_cuda_error",
-           "hk_constants", "hk_version", "hk_count_pairs", "hk_profile"]
+           "hk_constants", "hk_version", "hk_count_pairs", "hk_profile",
+           "hk_cross_section_noalloc"]
 
 
 class hk_lines(ctypes.Structure):
@@ -94,6 +96,8 @@ def lib():
     L.hk_count_pairs.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts),
                                  P(ctypes.c_int64), vp]
     L.hk_profile.argtypes = [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int64)]
+    L.hk_cross_section_noalloc.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts),
+                                           vp, vp]
     _lib = L
     return L
 
@@ -218,6 +222,18 @@ def hk_cross_section(lines: DeviceLines, grid: hk_grid, state: hk_state, opts: h
     _check("hk_cross_section", lib().hk_cross_section(ctypes.byref(L), ctypes.byref(grid),
                                                       ctypes.byref(state), ctypes.byref(opts),
                                                       _ptr(sigma_out), _stream(stream)))
+    return sigma_out
+
+
+def hk_cross_section_noalloc(lines: DeviceLines, grid: hk_grid, state: hk_state, opts: hk_opts,
+                             sigma_out: torch.Tensor, stream=None):
+    """hk_cross_section with its scratch in the library's fixed device array:
+    no device allocation by the library (the caller provides sigma_out)."""
+    L = lines.struct()
+    _check("hk_cross_section_noalloc",
+           lib().hk_cross_section_noalloc(ctypes.byref(L), ctypes.byref(grid),
+                                          ctypes.byref(state), ctypes.byref(opts),
+                                          _ptr(sigma_out), _stream(stream)))
     return sigma_out
 
 

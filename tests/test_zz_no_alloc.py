@@ -1,0 +1,68 @@
+"""hk_cross_section_noalloc: the cross section for callers that must not let
+the library allocate device memory (scratch in a fixed device array).
+
+Checked through the C ABI against hk_cross_section on the same inputs, twice
+in a row (the fixed array keeps the previous call's contents, so the second
+call shows that everything that must start at zero is cleared), in both
+precisions, plus the size and sortedness limits.  The file name sorts last so
+that a run stopping at the first failure has run every other test first.
+"""
+import numpy as np
+import pytest
+
+from parity import assert_sigma_close
+from paper_2101_02005_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+Q = synth.partition_function
+QREF = float(Q(296.0))
+
+
+@pytest.fixture(scope="module")
+def hk():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2101_02005_gb300 import build
+    build.build()
+    from paper_2101_02005_gb300 import hk
+    hk.lib()
+    return hk
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_matches_cross_section_twice(hk, prec):
+    # config-1 shape (log-normal density, 0.1 cm^-1 grid, 25 cm^-1 cut) at
+    # 1/1000 of its line count, then a second, different problem in a row
+    for call, (scale, T, P) in enumerate([(1e-3, 1500.0, 1.0), (2e-4, 800.0, 0.03)]):
+        w = synth.config(1, scale=scale)
+        L = w.species[0]
+        D = hk.DeviceLines.from_host(L)
+        grid = hk.make_grid(*w.grid.astuple())
+        st = hk.make_state(T, P, float(Q(T)))
+        op = hk.make_opts(QREF, w.cut, prec, flags=hk.HK_SIGMA_F64)
+        ref = hk.hk_cross_section(D, grid, st, op)
+        out = torch.full_like(ref, 12345.0)      # stale contents must not leak into sigma
+        hk.hk_cross_section_noalloc(D, grid, st, op, out)
+        hk.hk_sync_status()
+        assert_sigma_close(out.cpu().numpy(), ref.cpu().numpy(), f"noalloc call {call} prec={prec}")
+
+
+def test_noalloc_limits(hk):
+    L = synth.make_lines(100, 0.0, 50.0, 3, 18.0)
+    D = hk.DeviceLines.from_host(L)
+    st = hk.make_state(1000.0, 1.0, float(Q(1000.0)))
+    op = hk.make_opts(QREF, 5.0)
+    big = hk.make_grid(0.0, 1e-4, 3_000_000)         # FP32C needs ~24 MB > 16 MiB
+    out = torch.empty(8, dtype=torch.float32, device="cuda")
+    with pytest.raises(hk.HKError) as ei:
+        hk.hk_cross_section_noalloc(D, big, st, op, out)
+    assert ei.value.status == hk.HK_ESIZE
+    U = synth.make_lines(100, 0.0, 50.0, 3, 18.0, sort=False)
+    DU = hk.DeviceLines.from_host(U)
+    small = hk.make_grid(0.0, 0.01, 5000)
+    out = torch.empty(5000, dtype=torch.float32, device="cuda")
+    with pytest.raises(hk.HKError) as ei:
+        hk.hk_cross_section_noalloc(DU, small, st, op, out)
+    assert ei.value.status == hk.HK_ENOTSUP
