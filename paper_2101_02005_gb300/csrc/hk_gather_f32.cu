@@ -37,15 +37,20 @@ constexpr int TILE = 2048;        // bins per tile
 constexpr int QCAP = 64;          // core-queue entries per warp
 constexpr int FLUSH_ROUNDS = 2;   // rounds (32 lines per warp each) between two-sum folds
 
-// Per-line record, computed once per (line, item) by one lane.
+// Per-line record, computed once per (line, item) by one lane.  Groups are
+// aligned to absolute bin indices: group g holds bins [32 g, 32 g + 31], so a
+// tile (a multiple of 32 bins) is a contiguous range of groups and a line's
+// band segments are tile-independent group ranges.  Bands: gh1 (r2 >= 1.5e6),
+// gh2 (r2 >= 2500), gh4 (r2 >= 64), core (r2 < 64); a group takes the band
+// of its bin nearest the line centre.
 struct __align__(16) Rec {
     float b, rn, Y, s;          // x step per bin, centre offset from bin c, y^2, scaled strength
-    int c, lo, hi, pad;         // nearest bin to the centre, inclusive bin range in the cut
-    int kL2, kR2, kL3, kR3;     // offsets k = bin - c with r2 < 1.5e6 / 2500 (kL > kR: none)
-    int kL4, kR4, kLc, kRc;     // ... r2 < 200 / 64
-    float rnb, sy, sy2, Yq;     // rn b, s y / sqrt(pi), sy / 2, Y + 1/4          (2 nodes)
-    float C3, s23, s13, Ca;     // 3 Y + 9/4, 2 sy / 3, sy / 3                      (3 nodes)
-    float Cb, sa, sb, y;        // 2 tau Y + tau^2 for both 4-node pairs, 2 W sy    (4 nodes)
+    float rnb, sy, sy2, Yq;     // rn b, s y / sqrt(pi), sy / 2, Y + 1/4             (2 nodes)
+    float Ca, Cb, sa, sb;       // 2 tau Y + tau^2 for both 4-node pairs, 2 W sy      (4 nodes)
+    float y;                    // Gamma_L / alpha_D
+    int c, lo, hi;              // nearest bin to the centre, inclusive bin range in the cut
+    int gA, gB, L2, R2;         // the line's groups; groups of band gh2 or inner
+    int L4, R4, Lc, Rc;         // groups of band gh4 or inner; groups holding core bins
 };
 
 struct Smem {
@@ -59,19 +64,30 @@ struct Smem {
 constexpr float kTa = 0.27525512860841106f, kTb = 2.724744871391589f;   // 4-node tau
 constexpr float kWa = 2.0f * 0.4541241452319315f, kWb = 2.0f * 0.04587585476806851f;
 
-// Offsets k with |k - rn| < D, D = sqrt(R - Y) / b widened by a relative 1e-4
-// and 1e-3 bins so a bin on the edge takes the more accurate band.
-__device__ __forceinline__ void band_k(float R, float Y, float b, float rn, int *kL, int *kR)
+// Groups meeting the bins c + k, |k - rn| < D with D = sqrt(R - Y) / b (widened
+// by a relative 1e-4 and 1e-3 bins so an edge group takes the more accurate
+// band), nested in [Lp, Rp]; an empty band sits at Rp + 1.
+__device__ __forceinline__ void band_groups(float R, float Y, float b, float rn, int c, int Lp,
+                                            int Rp, int *L, int *R_)
 {
     const float d2 = R - Y;
-    if (!(d2 > 0.0f)) {
-        *kL = 1;
-        *kR = 0;
+    if (!(d2 > 0.0f) || Lp > Rp) {
+        *L = Rp + 1;
+        *R_ = Rp;
         return;
     }
     const float D = fminf(sqrtf(d2) / b * 1.0001f + 1e-3f, 1.0e9f);
-    *kL = (int)floorf(rn - D) + 1;
-    *kR = (int)ceilf(rn + D) - 1;
+    const int kL = (int)floorf(rn - D) + 1, kR = (int)ceilf(rn + D) - 1;
+    int lo = (c + kL) >> 5, hi = (c + kR) >> 5;   // arithmetic shifts: floor division
+    lo = max(lo, Lp);
+    hi = min(hi, Rp);
+    if (kL > kR || lo > hi) {
+        *L = Rp + 1;
+        *R_ = Rp;
+    } else {
+        *L = lo;
+        *R_ = hi;
+    }
 }
 
 __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t l, int scale,
@@ -89,7 +105,6 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
     q.lo = lo;
     q.hi = hi;
     q.rn = (float)rn;
-    q.pad = 0;
     float aDinv, y, sv;
     if (!any) {
         aDinv = 1.0f;
@@ -110,40 +125,25 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
     q.Y = Y;
     q.s = sv;
     q.y = y;
-    band_k(1.5e6f, Y, b, q.rn, &q.kL2, &q.kR2);
-    band_k(2500.0f, Y, b, q.rn, &q.kL3, &q.kR3);
-    band_k(200.0f, Y, b, q.rn, &q.kL4, &q.kR4);
-    band_k(64.0f, Y, b, q.rn, &q.kLc, &q.kRc);
     q.rnb = q.rn * b;
     q.sy = sy;
     q.sy2 = 0.5f * sy;
     q.Yq = Y + 0.25f;
-    q.C3 = fmaf(3.0f, Y, 2.25f);
-    q.s23 = sy * (2.0f / 3.0f);
-    q.s13 = sy * (1.0f / 3.0f);
     q.Ca = fmaf(2.0f * kTa, Y, kTa * kTa);
     q.Cb = fmaf(2.0f * kTb, Y, kTb * kTb);
     q.sa = sy * kWa;
     q.sb = sy * kWb;
-    *out = q;
-}
-
-// Groups whose nearest offset is inside [kL, kR], nested in [Lp, Rp].  Group g
-// covers offsets [ka + 32 g, ka + 32 g + 31]; it meets [kL, kR] iff
-// (kL - ka) >> 5 <= g <= (kR - ka) >> 5 (arithmetic shifts are floor
-// divisions).  An empty band sits at Rp + 1.
-__device__ __forceinline__ void band_groups(int kL, int kR, int ka, int Lp, int Rp, int *L, int *R)
-{
-    int lo = (kL - ka) >> 5, hi = (kR - ka) >> 5;
-    lo = max(lo, Lp);
-    hi = min(hi, Rp);
-    if (kL > kR || lo > hi) {
-        *L = Rp + 1;
-        *R = Rp;
+    if (any) {
+        q.gA = lo >> 5;
+        q.gB = hi >> 5;
     } else {
-        *L = lo;
-        *R = hi;
+        q.gA = 1;
+        q.gB = 0;
     }
+    band_groups(1.5e6f, Y, b, q.rn, c, q.gA, q.gB, &q.L2, &q.R2);
+    band_groups(2500.0f, Y, b, q.rn, c, q.L2, q.R2, &q.L4, &q.R4);
+    band_groups(64.0f, Y, b, q.rn, c, q.L4, q.R4, &q.Lc, &q.Rc);
+    *out = q;
 }
 
 // Value of one pair in band BAND at offset kf (float bin offset from c).
@@ -159,52 +159,36 @@ template <int BAND> __device__ __forceinline__ float pair_f(const Rec &q, float 
     } else if (BAND == kBandGH2) {          // |z^2 - 1/2|^2 = r2^2 - X + Y + 1/4
         const float d = fmaf(r2, r2, q.Yq - X);
         return __fdividef(fmaf(r2, q.sy, q.sy2), d);
-    } else if (BAND == kBandGH3) {          // |z^2 - 3/2|^2 = r2^2 - 3 X + 3 Y + 9/4
-        const float d = fmaf(r2, r2, fmaf(-3.0f, X, q.C3));
-        const float u = fmaf(r2, r2, 1.5f * r2);
-        return __fdividef(fmaf(q.s23, d, q.s13 * u), r2 * d);
-    } else {                                // both 4-node pairs
+    } else {                                // 4 nodes: |z^2 - tau|^2 = r2^2 - 2 tau (X - Y) + tau^2
         const float da = fmaf(r2, r2, fmaf(-2.0f * kTa, X, q.Ca));
         const float db = fmaf(r2, r2, fmaf(-2.0f * kTb, X, q.Cb));
         return __fdividef(fmaf(q.sa * (r2 + kTa), db, q.sb * (r2 + kTb) * da), da * db);
     }
 }
 
-// One band over groups [g0, g1) of a line.  `acc` points at the warp's tile
-// copy at the line's first bin plus this lane; `kf0` is this lane's offset in
-// group 0; groups below gf are full, group gf (if any) has `rem` live lanes.
+// One band over groups [g0, g1] (inclusive), clipped to [lo_g, hi_g].  A lane
+// adds only if its bin 32 g + lane lies in the line's range [lo, hi] (only the
+// line's first and last groups can be partial).  `base` is the warp's tile
+// copy at group tg0 plus this lane; kfc = lane - c.
 template <int BAND>
-__device__ __forceinline__ void sweep(const Rec &q, int g0, int g1, int gf, int rem, float *acc,
-                                      float kf0, int lane)
+__device__ __forceinline__ void sweep(const Rec &q, int g0, int g1, int lo_g, int hi_g, int tg0,
+                                      float *base, int kfc, int lane)
 {
-    const int gfull = min(g1, gf);
-    int g = g0;
-    float kf = kf0 + (float)(32 * g0);
-    float *p = acc + 32 * g0;
-    for (; g + 1 < gfull; g += 2, kf += 64.0f, p += 64) {
+    g0 = max(g0, lo_g);
+    g1 = min(g1, hi_g);
+    if (g0 > g1) return;
+    const unsigned span = (unsigned)(q.hi - q.lo);
+    unsigned rel = (unsigned)(32 * g0 + lane - q.lo);   // bin - lo
+    float kf = (float)(32 * g0 + kfc);
+    float *p = base + 32 * (g0 - tg0);
+    float *pe = base + 32 * (g1 - tg0);
+    for (; p < pe; p += 64, kf += 64.0f, rel += 64u) {   // two groups per step
         const float v0 = pair_f<BAND>(q, kf);
         const float v1 = pair_f<BAND>(q, kf + 32.0f);
-        p[0] += v0;
-        p[32] += v1;
+        if (rel <= span) p[0] += v0;
+        if (rel + 32u <= span) p[32] += v1;
     }
-    if (g < gfull) {
-        p[0] += pair_f<BAND>(q, kf);
-        ++g;
-        kf += 32.0f;
-        p += 32;
-    }
-    if (g1 > gf && g0 <= gf && lane < rem) {   // the partial last group
-        const float kfl = kf0 + (float)(32 * gf);
-        acc[32 * gf] += pair_f<BAND>(q, kfl);
-    }
-}
-
-template <int BAND>
-__device__ __forceinline__ void sweep2(const Rec &q, int a0, int a1, int b0, int b1, int gf,
-                                       int rem, float *acc, float kf0, int lane)
-{
-    if (a0 < a1) sweep<BAND>(q, a0, a1, gf, rem, acc, kf0, lane);
-    if (b0 < b1) sweep<BAND>(q, b0, b1, gf, rem, acc, kf0, lane);
+    if (p == pe && rel <= span) p[0] += pair_f<BAND>(q, kf);
 }
 
 __device__ __forceinline__ void core_entry(Smem &S, int warp, int t0, unsigned e)
@@ -216,25 +200,28 @@ __device__ __forceinline__ void core_entry(Smem &S, int warp, int t0, unsigned e
     atomicAdd(&S.acc[warp][tidx], qq.s * core_re<float>(xx, qq.y));
 }
 
-// Central groups [g0, g1): bins with r2 >= 64 take the 4-node rule in place,
-// core bins (r2 < 64) are queued as (record slot, tile index) and evaluated
-// 32 at a time.
-__device__ __forceinline__ void sweep_core(const Rec &q, int slot, int g0, int g1, int nact,
-                                           float *acc0, float kf0, int lane, int tidx0,
+// Groups holding core bins: lanes with r2 >= 64 take the 4-node rule (valid
+// for every r2 >= 64) in place; core lanes (r2 < 64) are queued as (record
+// slot, tile index) and the queue is evaluated 32 entries at a time with the
+// trapezoid rule.
+__device__ __forceinline__ void sweep_core(const Rec &q, int slot, int g0, int g1, int lo_g,
+                                           int hi_g, int tg0, float *base, int kfc, int lane,
                                            unsigned *queue, int &qn, Smem &S, int warp, int t0)
 {
-    int off = 32 * g0 + lane;
-    float kf = kf0 + (float)(32 * g0);
-    for (int gi = g0; gi < g1; ++gi, off += 32, kf += 32.0f) {
-        const bool act = off < nact;
+    g0 = max(g0, lo_g);
+    g1 = min(g1, hi_g);
+    const unsigned span = (unsigned)(q.hi - q.lo);
+    for (int g = g0; g <= g1; ++g) {
+        const bool act = (unsigned)(32 * g + lane - q.lo) <= span;
+        const float kf = (float)(32 * g + kfc);
         const float x = fmaf(kf, q.b, -q.rnb);
         const float r2 = fmaf(x, x, q.Y);
         const bool core = act && r2 < 64.0f;
-        if (act && !core) acc0[off] += pair_f<kBandGH4>(q, kf);
+        if (act && !core) base[32 * (g - tg0)] += pair_f<kBandGH4>(q, kf);
         const unsigned m = __ballot_sync(0xffffffffu, core);
         if (m) {
             const int pos = qn + __popc(m & ((1u << lane) - 1u));
-            if (core) queue[pos] = ((unsigned)slot << 16) | (unsigned)(tidx0 + off);
+            if (core) queue[pos] = ((unsigned)slot << 16) | (unsigned)(32 * g + lane - t0);
             qn += __popc(m);
             __syncwarp();
             if (qn >= 32) {
@@ -256,6 +243,24 @@ __device__ __forceinline__ void drain_rest(unsigned *queue, int &qn, Smem &S, in
         qn = 0;
     }
     __syncwarp();
+}
+
+// All of one line's bins inside the tile (groups [tg0, tg1]).
+__device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1, float *base,
+                                        int lane, unsigned *queue, int &qn, Smem &S, int warp,
+                                        int t0)
+{
+    const int ga = max(q.gA, tg0), gb = min(q.gB, tg1);
+    if (ga > gb) return;  // warp-uniform
+    const int kfc = lane - q.c;
+    sweep<kBandGH1>(q, q.gA, q.L2 - 1, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH2>(q, q.L2, q.L4 - 1, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH4>(q, q.L4, q.Lc - 1, ga, gb, tg0, base, kfc, lane);
+    if (q.Lc <= q.Rc)
+        sweep_core(q, slot, q.Lc, q.Rc, ga, gb, tg0, base, kfc, lane, queue, qn, S, warp, t0);
+    sweep<kBandGH4>(q, q.Rc + 1, q.R4, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH2>(q, q.R4 + 1, q.R2, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH1>(q, q.R2 + 1, q.gB, ga, gb, tg0, base, kfc, lane);
 }
 
 __device__ __forceinline__ void fold(Smem &S, int tid)
@@ -318,42 +323,29 @@ __global__ void __launch_bounds__(NT, 2)
         const int64_t l_begin = s_lb, l_end = s_le;
         const Prob &pr = probs[p];
         const int scale = *pr.scale_exp;
+        const int tg0 = t0 >> 5, tg1 = t1 >> 5;           // the tile's groups
+        float *accb = &S.acc[warp][0] + lane;
         int rounds = 0;
         for (int64_t base = l_begin; base < l_end; base += NT) {
             const int64_t l = base + tid;  // warp w owns lines base + 32 w + lane
             Rec q;
             if (l < l_end) {
                 make_rec(pr, g, l, scale, &q);
-            } else {
+            } else {  // past the item's lines: an empty record
                 q.lo = 0x3fffffff;
                 q.hi = -0x3fffffff;
+                q.gA = 1;
+                q.gB = 0;
             }
             S.rec[warp][lane] = q;
             __syncwarp();
             int qn = 0;
-            for (int j = 0; j < 32; ++j) {
-                const Rec &r = S.rec[warp][j];
-                const int a = max(r.lo, t0), bb = min(r.hi, t1);
-                if (a > bb) continue;  // warp-uniform
-                const Rec q2 = r;
-                const int ka = a - q2.c;
-                const int nact = bb - a + 1;
-                const int G = (nact + 31) >> 5, gf = nact >> 5, rem = nact & 31;
-                int L2, R2, L3, R3, L4, R4, Lc, Rc;
-                band_groups(q2.kL2, q2.kR2, ka, 0, G - 1, &L2, &R2);
-                band_groups(q2.kL3, q2.kR3, ka, L2, R2, &L3, &R3);
-                band_groups(q2.kL4, q2.kR4, ka, L3, R3, &L4, &R4);
-                band_groups(q2.kLc, q2.kRc, ka, L4, R4, &Lc, &Rc);
-                float *acc0 = &S.acc[warp][a - t0];
-                float *acc = acc0 + lane;
-                const float kf0 = (float)(ka + lane);
-                sweep2<kBandGH1>(q2, 0, L2, R2 + 1, G, gf, rem, acc, kf0, lane);
-                sweep2<kBandGH2>(q2, L2, L3, R3 + 1, R2 + 1, gf, rem, acc, kf0, lane);
-                sweep2<kBandGH3>(q2, L3, L4, R4 + 1, R3 + 1, gf, rem, acc, kf0, lane);
-                sweep2<kBandGH4>(q2, L4, Lc, Rc + 1, R4 + 1, gf, rem, acc, kf0, lane);
-                if (Lc <= Rc)
-                    sweep_core(q2, j, Lc, Rc + 1, nact, acc0, kf0, lane, a - t0, queue, qn, S,
-                               warp, t0);
+            for (int j = 0; j < 32; ++j)
+            {
+                // a register copy: the record must not be re-read from shared
+                // memory after every store into the tile copy
+                const Rec q = S.rec[warp][j];
+                do_line(q, j, tg0, tg1, accb, lane, queue, qn, S, warp, t0);
             }
             drain_rest(queue, qn, S, warp, lane, t0);
             if (++rounds == FLUSH_ROUNDS) {

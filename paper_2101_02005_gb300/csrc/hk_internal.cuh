@@ -122,6 +122,30 @@ template <> struct Math<double> {
      7.81148940830449097e-07, 1.43072419185676882e-08, 1.58939100945163677e-10,              \
      1.07092323825080766e-12, 4.37661850287085020e-15}
 
+// sin(pi a), cos(pi a) for the float core: exact reduction a = n + f with
+// |f| <= 1/2 (a - rint(a) is exact), then the hardware sine and cosine of
+// pi f (absolute error ~4e-7 on [-pi/2, pi/2]) and the sign of n's parity.
+__device__ __forceinline__ void sincospi_core(float a, float *s, float *c)
+{
+    const float n = rintf(a);
+    const float f = a - n;
+    float sf, cf;
+    __sincosf((float)kPI * f, &sf, &cf);
+    const bool odd = ((int)n) & 1;
+    *s = odd ? -sf : sf;
+    *c = odd ? -cf : cf;
+}
+
+// sin, cos of a >= 0 for the float core: a = 2 pi k + r with r in [-pi, pi]
+// (2 pi split in two floats so the reduction keeps ~1e-7 absolute), then the
+// hardware sine and cosine.
+__device__ __forceinline__ void sincos_core(float a, float *s, float *c)
+{
+    const float k = rintf(a * (float)(0.5 * kInvPi));
+    const float r = fmaf(-k, 6.28318548202514648f, fmaf(-k, -1.7484556e-7f, a));
+    __sincosf(r, s, c);
+}
+
 // Re w(x + iy) for r2 < 64 (any x sign; uses |x|).
 template <typename R> __device__ __forceinline__ R core_re(R x, R y)
 {
@@ -147,13 +171,23 @@ template <typename R> __device__ __forceinline__ R core_re(R x, R y)
         R em = Math<R>::expm1_(R(4 * kPI) * y);  // e^eta - 1
         R E = R(1) + em;
         R sn, cs;
-        Math<R>::sincospi_(R(4) * ax, &sn, &cs);
+        R s2, c2;
+        if (sizeof(R) == 4) {
+            float sf, cf, s2f, c2f;
+            sincospi_core((float)(R(4) * ax), &sf, &cf);
+            sincos_core((float)(R(2) * ax * y), &s2f, &c2f);
+            sn = (R)sf;
+            cs = (R)cf;
+            s2 = (R)s2f;
+            c2 = (R)c2f;
+        } else {
+            Math<R>::sincospi_(R(4) * ax, &sn, &cs);
+            Math<R>::sincos_(R(2) * ax * y, &s2, &c2);
+        }
         if (sh) {                          // theta + pi for the shifted lattice
             sn = -sn;
             cs = -cs;
         }
-        R s2, c2;
-        Math<R>::sincos_(R(2) * ax * y, &s2, &c2);
         R num = c2 * (R(1) - E * cs) - s2 * E * sn;
         R den = em * em + R(2) * E * (R(1) - cs);
         re += R(2) * Math<R>::exp_(Y - ax * ax) * num / den;

@@ -6,7 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 
-#include "../../include/hk.h"
+#include "hk.h"
 #include "hk_internal.cuh"
 
 namespace hk {
