@@ -33,6 +33,10 @@ METRIC = "lines/s and Voigt evals/s on 1 GB300 (FP32-comp vs FP64 GPU) at stated
 # shared x, x^2, r^2 and accumulate = 6; band formulas add 2 / 8 / 13 / 19
 # and ~194 for the trapezoid core.  Band counts come from hk_count_pairs.
 FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 19, "gh4": 25, "core": 200}
+# DRAM bytes per line of one k_gather_f32 launch, from the ncu capture in
+# profiles/k_gather_f32_config1-1e7-lines.md (248.1 MB for 1e7 lines; traffic
+# grows with the line count).  Set to None when the kernel changes.
+GATHER_DRAM_BYTES_PER_LINE = 24.81
 FP32_LANES_PER_SM = 128
 
 
@@ -287,9 +291,11 @@ def main():
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     g_ms = gather_ms / max(gather_launches, 1)
     achieved = flops_step / (g_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": "k_gather<float,4>", "achieved": achieved,
+    traffic = (GATHER_DRAM_BYTES_PER_LINE * L.n
+               if GATHER_DRAM_BYTES_PER_LINE and args.config == 1 else None)
+    roofline = {"bound": "alu", "kernel": "k_gather_f32", "achieved": achieved,
                 "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                "traffic": None, "gather_ms_per_launch": g_ms,
+                "traffic": traffic, "algorithmic_bytes": 24 * L.n, "gather_ms_per_launch": g_ms,
                 "gather_share_of_step": g_ms / ms_step if ms_step else None,
                 "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
                               f"{sm_max:.0f} MHz (derived, FP32 FMA)",

@@ -536,7 +536,8 @@ int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt,
             return fail_cuda(e);
         // INT_MIN in every scale slot: 0x80 bytes give 0x80808080 < any real exponent
         if ((e = cudaMemsetAsync(scales, 0x80, sizeof(int) * nprob, st))) return fail_cuda(e);
-        dim3 grid(num_sms * 2, nprob);
+        // enough warps in flight to keep the line reads at HBM speed
+        dim3 grid(num_sms * 16, nprob);
         k_scale_prepass<<<grid, 256, 0, st>>>(probs_d, nprob, g);
         if ((e = cudaGetLastError())) return fail_cuda(e);
     } else if (!accumulate) {
