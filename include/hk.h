@@ -244,11 +244,19 @@ int hk_cross_section_backward(const hk_lines *lines, const hk_grid *grid, const 
 int hk_workspace_size(int kind, const hk_lines *species, int nspecies, int nTP,
                       const hk_grid *grid, const hk_opts *opts, size_t *bytes);
 
-/* Times the gather kernel's tuning candidates (bins per thread, lines per
- * work item) on a short slice of this problem and caches the fastest for
- * the current device and problem class.  Synchronises `stream`. */
+/* The self-tuning of Sect. 2.4.4 (the paper re-tunes its thread counts
+ * during a run), done once: times the Voigt sum of this problem for each
+ * candidate number of lines per work item (2048 ... 131072; small items
+ * balance uneven line density, large ones amortise per-item costs) and
+ * caches the fastest for the current device and opts->precision; later
+ * calls, batched ones included, use it.  Runs the problem eight times and
+ * synchronises `stream`.  Allocates one nbins-sized buffer while it runs. */
 int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
                 const hk_opts *opts, void *stream);
+
+/* The lines-per-item setting in use for a precision (the default 16384 until
+ * hk_autotune has run on this device).  lmax: HOST int. */
+int hk_tuning(int precision, int *lmax);
 
 /* Instrumentation (no counterpart in the paper).  Counts the (line, bin)
  * pairs the cut admits for this problem: counts[0] = total (the algorithmic

@@ -193,6 +193,7 @@ void hko_line_strength(int64_t n, const double *nu0, const double *S_ref, const 
 {
     const double c2 = O_H * O_C / O_KB;
     const double m_g = mass_amu * O_AMU;
+#pragma omp parallel for schedule(static)
     for (int64_t l = 0; l < n; ++l) {
         double S;
         if (s_mode == 0) {
@@ -216,6 +217,7 @@ void hko_widths(int64_t n, const double *nu0, const double *gamma_ref, const dou
                 double mass_amu, double *alphaD_out, double *gammaL_out)
 {
     const double m_g = mass_amu * O_AMU;
+#pragma omp parallel for schedule(static)
     for (int64_t l = 0; l < n; ++l) {
         alphaD_out[l] = nu0[l] / O_C * sqrt(2.0 * O_KB * T / m_g);
         double nat = A ? A[l] / (4.0 * O_PI * O_C) : 0.0;
@@ -288,6 +290,7 @@ static void line_range(double nu0, double nu_min, double dnu, int64_t nbins, dou
 void hko_line_ranges(int64_t n, const double *nu0, double nu_min, double dnu, int64_t nbins,
                      double cut, int64_t *lo, int64_t *hi)
 {
+#pragma omp parallel for schedule(static)
     for (int64_t l = 0; l < n; ++l)
         line_range(nu0[l], nu_min, dnu, nbins, cut, &lo[l], &hi[l]);
 }
@@ -296,6 +299,7 @@ int64_t hko_count_pairs(int64_t n, const double *nu0, double nu_min, double dnu,
                         double cut)
 {
     int64_t total = 0;
+#pragma omp parallel for schedule(static) reduction(+ : total)
     for (int64_t l = 0; l < n; ++l) {
         int64_t lo, hi;
         line_range(nu0[l], nu_min, dnu, nbins, cut, &lo, &hi);

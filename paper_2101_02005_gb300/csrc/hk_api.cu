@@ -723,9 +723,11 @@ int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *stat
     if (lines->n == 0) return HK_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const int prec = opts->precision;
-    const int bpts_f[] = {2, 4, 8};
-    const int bpts_d[] = {2};
-    const int lmaxs[] = {4096, 16384, 65536};
+    const int bpt = get_tune(prec).bpt;
+    // lines per work item: small items balance uneven line density across the
+    // SMs, large ones cut the per-item cost (record setup, one FP64 atomic per
+    // bin of the tile)
+    const int lmaxs[] = {2048, 8192, 32768, 131072};
     size_t out_b = (size_t)grid->nbins * 8;
     // the output buffer lives in its own cudaMalloc (the pool is used by the runs)
     void *out = nullptr;
@@ -736,31 +738,29 @@ int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *stat
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    Tune best;
+    hk_opts o = *opts;
+    o.flags |= HK_SIGMA_F64;  // time without any float-overflow concern
+    Tune best = get_tune(prec);
     float best_ms = 1e30f;
-    const int *bp = prec == HK_FP64 ? bpts_d : bpts_f;
-    int nb = prec == HK_FP64 ? 1 : 3;
-    for (int i = 0; i < nb && rc == HK_OK; ++i)
-        for (int j = 0; j < 3 && rc == HK_OK; ++j) {
-            // one warm-up, then one timed run
-            rc = cross_section_impl(lines, grid, state, opts, out, st, bp[i], lmaxs[j]);
-            if (rc) break;
-            cudaEventRecord(e0, st);
-            rc = cross_section_impl(lines, grid, state, opts, out, st, bp[i], lmaxs[j]);
-            cudaEventRecord(e1, st);
-            if (rc) break;
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                rc = fail_cuda(cudaGetLastError());
-                break;
-            }
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms) {
-                best_ms = ms;
-                best.bpt = bp[i];
-                best.lmax = lmaxs[j];
-            }
+    for (int j = 0; j < 4 && rc == HK_OK; ++j) {
+        rc = cross_section_impl(lines, grid, state, &o, out, st, bpt, lmaxs[j]);  // warm-up
+        if (rc) break;
+        cudaEventRecord(e0, st);
+        rc = cross_section_impl(lines, grid, state, &o, out, st, bpt, lmaxs[j]);
+        cudaEventRecord(e1, st);
+        if (rc) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = fail_cuda(cudaGetLastError());
+            break;
         }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best.bpt = bpt;
+            best.lmax = lmaxs[j];
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamSynchronize(st);
@@ -770,6 +770,13 @@ int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *stat
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[{dev, prec}] = best;
+    return HK_OK;
+}
+
+int hk_tuning(int precision, int *lmax)
+{
+    if ((precision != HK_FP32C && precision != HK_FP64) || !lmax) return HK_EINVAL;
+    *lmax = get_tune(precision).lmax;
     return HK_OK;
 }
 

@@ -239,11 +239,10 @@ int backward_run(Prob *probs_h, int nTP, const GridD &g, const float *grad_sigma
         hs[2 * k] = T[k];
         hs[2 * k + 1] = dlnQ_dT[k];
     }
-    // pageable sources: both copies are staged before cudaMemcpyAsync returns
     cudaError_t e;
-    e = cudaMemcpyAsync(probs_d, probs_h, sizeof(Prob) * nTP, cudaMemcpyHostToDevice, st);
-    if (!e) e = cudaMemcpyAsync(kscal, hs.data(), sizeof(double) * 2 * nTP, cudaMemcpyHostToDevice, st);
-    if (e) return fail_cuda(e);
+    int urc = upload_probs(probs_d, probs_h, nTP, st);
+    if (!urc) urc = upload_doubles(kscal, hs.data(), 2 * nTP, st);
+    if (urc) return urc;
     if ((e = cudaMemsetAsync(dL_dT, 0, sizeof(double) * nTP, st))) return fail_cuda(e);
     if ((e = cudaMemsetAsync(dL_dP, 0, sizeof(double) * nTP, st))) return fail_cuda(e);
     int64_t n = probs_h[0].n;

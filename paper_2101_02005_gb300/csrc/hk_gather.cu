@@ -470,6 +470,57 @@ int gather_profile(int mode, double *ms, int64_t *launches)
     return rc;
 }
 
+// ---- descriptor upload through kernel parameters ------------------------------
+// Problem descriptors reach the device as kernel arguments (64 per launch,
+// ~13 KB of parameters) instead of a copy from pageable host memory, so every
+// call is a plain sequence of kernel launches and memsets: it can be captured
+// into a CUDA graph and the host array may be freed as soon as the call returns.
+constexpr int kProbsPerUpload = 64;
+struct ProbChunk {
+    Prob p[kProbsPerUpload];
+    int n;
+};
+__global__ void k_store_probs(Prob *dst, const ProbChunk chunk)
+{
+    for (int i = threadIdx.x; i < chunk.n; i += blockDim.x) dst[i] = chunk.p[i];
+}
+
+constexpr int kDoublesPerUpload = 512;
+struct DoubleChunk {
+    double v[kDoublesPerUpload];
+    int n;
+};
+__global__ void k_store_doubles(double *dst, const DoubleChunk chunk)
+{
+    for (int i = threadIdx.x; i < chunk.n; i += blockDim.x) dst[i] = chunk.v[i];
+}
+
+int upload_probs(Prob *dst, const Prob *src, int n, cudaStream_t st)
+{
+    for (int off = 0; off < n; off += kProbsPerUpload) {
+        ProbChunk c;
+        c.n = n - off < kProbsPerUpload ? n - off : kProbsPerUpload;
+        for (int i = 0; i < c.n; ++i) c.p[i] = src[off + i];
+        k_store_probs<<<1, kProbsPerUpload, 0, st>>>(dst + off, c);
+        cudaError_t e = cudaGetLastError();
+        if (e) return fail_cuda(e);
+    }
+    return HK_OK;
+}
+
+int upload_doubles(double *dst, const double *src, int n, cudaStream_t st)
+{
+    for (int off = 0; off < n; off += kDoublesPerUpload) {
+        DoubleChunk c;
+        c.n = n - off < kDoublesPerUpload ? n - off : kDoublesPerUpload;
+        for (int i = 0; i < c.n; ++i) c.v[i] = src[off + i];
+        k_store_doubles<<<1, 256, 0, st>>>(dst + off, c);
+        cudaError_t e = cudaGetLastError();
+        if (e) return fail_cuda(e);
+    }
+    return HK_OK;
+}
+
 // ---- host side ----------------------------------------------------------------
 
 int gather_tile_bins(int precision, int bpt)
@@ -528,8 +579,8 @@ int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt,
         else probs_h[p].acc = (double *)out + (size_t)p * g.nbins;
     }
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(probs_d, probs_h, sizeof(Prob) * nprob, cudaMemcpyHostToDevice, st)))
-        return fail_cuda(e);
+    int urc = upload_probs(probs_d, probs_h, nprob, st);
+    if (urc) return urc;
     if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long) * 2, st))) return fail_cuda(e);
     if (precision == 0) {
         if ((e = cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)nprob * g.nbins, st)))

@@ -14,6 +14,11 @@ namespace hk {
 // Records a CUDA error for hk_last_cuda_error() and returns HK_ECUDA.
 int fail_cuda(cudaError_t e);
 
+// Host arrays to device memory through kernel parameters (stream-ordered,
+// capturable, no pageable-memory copy).
+int upload_probs(Prob *dst, const Prob *src, int n, cudaStream_t st);
+int upload_doubles(double *dst, const double *src, int n, cudaStream_t st);
+
 // Gather (hk_gather.cu).  Tile width in bins for a precision / bins-per-thread.
 int gather_tile_bins(int precision, int bpt);
 // Workspace bytes of gather_run for nprob sigma arrays of nbins bins.

@@ -27,7 +27,7 @@ EXPORTS = ["hk_line_strength", "hk_widths", "hk_voigt_accumulate", "hk_cross_sec
            "hk_cross_section_batched", "hk_cross_section_backward", "hk_workspace_size",
            "hk_autotune", "hk_sync_status", "hk_release", "hk_strerror", "hk_last_cuda_error",
            "hk_constants", "hk_version", "hk_count_pairs", "hk_profile",
-           "hk_cross_section_noalloc"]
+           "hk_cross_section_noalloc", "hk_tuning"]
 
 
 class hk_lines(ctypes.Structure):
@@ -96,6 +96,7 @@ def lib():
     L.hk_count_pairs.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts),
                                  P(ctypes.c_int64), vp]
     L.hk_profile.argtypes = [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int64)]
+    L.hk_tuning.argtypes = [ctypes.c_int, P(ctypes.c_int)]
     L.hk_cross_section_noalloc.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts),
                                            vp, vp]
     _lib = L
@@ -313,6 +314,13 @@ def hk_profile(mode: int):
     n = ctypes.c_int64(0)
     _check("hk_profile", lib().hk_profile(int(mode), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, int(n.value)
+
+
+def hk_tuning(precision: int = HK_FP32C) -> int:
+    """Lines per work item currently used for `precision`."""
+    v = ctypes.c_int(0)
+    _check("hk_tuning", lib().hk_tuning(int(precision), ctypes.byref(v)))
+    return int(v.value)
 
 
 def hk_sync_status(stream=None):

@@ -246,3 +246,48 @@ def test_backward_matches_oracle_gradient(hk):
         assert abs(dP[k] - oP) <= 1e-4 * abs(oP), (k, dP[k], oP)
     assert np.linalg.norm(dS - oS) <= 1e-4 * np.linalg.norm(oS)
     assert np.linalg.norm(dG - oG) <= 1e-4 * np.linalg.norm(oG)
+
+
+def test_batched_graph_capture_replay(hk):
+    """The batched call is a plain sequence of kernel launches and memsets:
+    captured once into a CUDA graph and replayed, it gives the direct result."""
+    w = synth.config(3, scale=1e-4)
+    grid = hk.make_grid(0.0, 0.01, 100000)
+    species = [hk.DeviceLines.from_host(s) for s in w.species]
+    states = [hk.make_state(t, p, float(Q(t))) for t in w.T[::10] for p in w.P[::5]]
+    opts = hk.make_opts(QREF, w.cut, flags=hk.HK_SIGMA_F64)
+    need = hk.hk_workspace_size(0, species, len(states), grid, opts)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    out = torch.empty((len(species), len(states), grid.nbins), dtype=torch.float64, device="cuda")
+    direct = hk.hk_cross_section_batched(species, states, grid, opts, out, ws).clone()
+    hk.hk_sync_status()
+    out.zero_()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            hk.hk_cross_section_batched(species, states, grid, opts, out, ws, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        out.zero_()
+        g.replay()
+    torch.cuda.synchronize()
+    a, b = out.cpu().numpy(), direct.cpu().numpy()
+    assert np.allclose(a, b, rtol=1e-12, atol=0)
+    assert np.count_nonzero(a) > 0.5 * a.size
+
+
+def test_autotune_keeps_results(hk):
+    L = synth.config(1, scale=2e-4).species[0]
+    w = synth.config(1, scale=2e-4)
+    D = hk.DeviceLines.from_host(L)
+    T, P = w.states()[0]
+    args = (D, hk.make_grid(*w.grid.astuple()), hk.make_state(T, P, float(Q(T))),
+            hk.make_opts(QREF, w.cut, flags=hk.HK_SIGMA_F64))
+    before = hk.hk_cross_section(*args).cpu().numpy()
+    hk.hk_autotune(*args)
+    assert hk.hk_tuning(hk.HK_FP32C) in (2048, 8192, 32768, 131072)
+    after = hk.hk_cross_section(*args).cpu().numpy()
+    hk.hk_sync_status()
+    assert_sigma_close(after, before, "after autotune")
