@@ -33,7 +33,7 @@ namespace f32g {
 
 constexpr int NW = 8;             // warps per block
 constexpr int NT = NW * 32;
-constexpr int TILE = 2048;        // bins per tile
+constexpr int TILE = 1024;        // bins per tile
 constexpr int QCAP = 64;          // core-queue entries per warp
 constexpr int FLUSH_ROUNDS = 2;   // rounds (32 lines per warp each) between two-sum folds
 
@@ -279,7 +279,7 @@ __device__ __forceinline__ void fold(Smem &S, int tid)
     }
 }
 
-__global__ void __launch_bounds__(NT, 2)
+__global__ void __launch_bounds__(NT, 3)
     k_gather_f32(const Prob *__restrict__ probs, GridD g, int64_t ntiles, int64_t m,
                  const int64_t *__restrict__ item_off, const int64_t *__restrict__ tile_lb,
                  const int64_t *__restrict__ tile_le, int lmax, unsigned long long *counter)
