@@ -8,7 +8,7 @@
 //   parameters of line i once (bin geometry in FP64, strength and widths in
 //   FP32, band boundaries) into a per-warp record table; then the warp sweeps
 //   each line's bins inside the tile, 32 consecutive bins per step (lane =
-//   bin), so no lane ever tests whether its bin is inside the cut.
+//   bin); only the line's first and last groups are masked against the cut.
 // * The Faddeeva band of a 32-bin group is the band of its bin nearest the
 //   line centre.  The bands form nested intervals of group indices around
 //   the centre, computed once per line, so each group runs one formula with
@@ -152,43 +152,79 @@ template <int BAND> __device__ __forceinline__ float pair_f(const Rec &q, float 
     const float x = fmaf(kf, q.b, -q.rnb);
     const float X = x * x;
     const float r2 = X + q.Y;
-    // __fdividef: one reciprocal and a multiply, within 2 ulp while the
-    // divisor is below 2^126 (gh1 beyond that gives 0, far below any sum)
+    // one hardware reciprocal and a multiply, within 2 ulp while the divisor
+    // is below 2^126 (gh1 beyond that gives 0, far below any sum)
     if (BAND == kBandGH1) {
-        return __fdividef(q.sy, r2);
+        return q.sy * rcp_ftz(r2);
     } else if (BAND == kBandGH2) {          // |z^2 - 1/2|^2 = r2^2 - X + Y + 1/4
         const float d = fmaf(r2, r2, q.Yq - X);
-        return __fdividef(fmaf(r2, q.sy, q.sy2), d);
+        return fmaf(r2, q.sy, q.sy2) * rcp_ftz(d);
     } else {                                // 4 nodes: |z^2 - tau|^2 = r2^2 - 2 tau (X - Y) + tau^2
         const float da = fmaf(r2, r2, fmaf(-2.0f * kTa, X, q.Ca));
         const float db = fmaf(r2, r2, fmaf(-2.0f * kTb, X, q.Cb));
-        return __fdividef(fmaf(q.sa * (r2 + kTa), db, q.sb * (r2 + kTb) * da), da * db);
+        return fmaf(q.sa * (r2 + kTa), db, q.sb * (r2 + kTb) * da) * rcp_ftz(da * db);
     }
 }
 
-// One band over groups [g0, g1] (inclusive), clipped to [lo_g, hi_g].  A lane
-// adds only if its bin 32 g + lane lies in the line's range [lo, hi] (only the
-// line's first and last groups can be partial).  `base` is the warp's tile
-// copy at group tg0 plus this lane; kfc = lane - c.
+// One masked group: lanes add only where bin 32 g + lane lies in the line's
+// range [lo, hi].
 template <int BAND>
+__device__ __forceinline__ void edge_group(const Rec &q, int g, int tg0, float *base, int kfc,
+                                           int lane)
+{
+    if ((unsigned)(32 * g + lane - q.lo) <= (unsigned)(q.hi - q.lo))
+        base[32 * (g - tg0)] += pair_f<BAND>(q, (float)(32 * g + kfc));
+}
+
+// One band over groups [g0, g1] (inclusive), clipped to [lo_g, hi_g].  `base`
+// is the warp's tile copy at group tg0 plus this lane; kfc = lane - c.  Only
+// the line's first and last groups (gA, gB) can be partial.  PEEL = false: a
+// lane adds only if its bin lies in the line's range (one compare per group,
+// best for lines a few groups wide); PEEL = true: gA and gB are peeled off
+// and masked, the groups between them run unmasked (best for wide lines,
+// where the per-band test costs less than the per-group one).
+template <int BAND, bool PEEL>
 __device__ __forceinline__ void sweep(const Rec &q, int g0, int g1, int lo_g, int hi_g, int tg0,
                                       float *base, int kfc, int lane)
 {
     g0 = max(g0, lo_g);
     g1 = min(g1, hi_g);
     if (g0 > g1) return;
-    const unsigned span = (unsigned)(q.hi - q.lo);
-    unsigned rel = (unsigned)(32 * g0 + lane - q.lo);   // bin - lo
-    float kf = (float)(32 * g0 + kfc);
-    float *p = base + 32 * (g0 - tg0);
-    float *pe = base + 32 * (g1 - tg0);
-    for (; p < pe; p += 64, kf += 64.0f, rel += 64u) {   // two groups per step
-        const float v0 = pair_f<BAND>(q, kf);
-        const float v1 = pair_f<BAND>(q, kf + 32.0f);
-        if (rel <= span) p[0] += v0;
-        if (rel + 32u <= span) p[32] += v1;
+    float kf;
+    float *p, *pe;
+    if (PEEL) {
+        if (g0 == q.gA) {
+            edge_group<BAND>(q, g0, tg0, base, kfc, lane);
+            if (++g0 > g1) return;
+        }
+        if (g1 == q.gB) {
+            edge_group<BAND>(q, g1, tg0, base, kfc, lane);
+            if (--g1 < g0) return;
+        }
+        kf = (float)(32 * g0 + kfc);
+        p = base + 32 * (g0 - tg0);
+        pe = base + 32 * (g1 - tg0);
+        for (; p < pe; p += 64, kf += 64.0f) {   // two groups per step
+            const float v0 = pair_f<BAND>(q, kf);
+            const float v1 = pair_f<BAND>(q, kf + 32.0f);
+            p[0] += v0;
+            p[32] += v1;
+        }
+        if (p == pe) p[0] += pair_f<BAND>(q, kf);
+    } else {
+        const unsigned span = (unsigned)(q.hi - q.lo);
+        unsigned rel = (unsigned)(32 * g0 + lane - q.lo);   // bin - lo
+        kf = (float)(32 * g0 + kfc);
+        p = base + 32 * (g0 - tg0);
+        pe = base + 32 * (g1 - tg0);
+        for (; p < pe; p += 64, kf += 64.0f, rel += 64u) {   // two groups per step
+            const float v0 = pair_f<BAND>(q, kf);
+            const float v1 = pair_f<BAND>(q, kf + 32.0f);
+            if (rel <= span) p[0] += v0;
+            if (rel + 32u <= span) p[32] += v1;
+        }
+        if (p == pe && rel <= span) p[0] += pair_f<BAND>(q, kf);
     }
-    if (p == pe && rel <= span) p[0] += pair_f<BAND>(q, kf);
 }
 
 __device__ __forceinline__ void core_entry(Smem &S, int warp, int t0, unsigned e)
@@ -246,6 +282,7 @@ __device__ __forceinline__ void drain_rest(unsigned *queue, int &qn, Smem &S, in
 }
 
 // All of one line's bins inside the tile (groups [tg0, tg1]).
+template <bool PEEL>
 __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1, float *base,
                                         int lane, unsigned *queue, int &qn, Smem &S, int warp,
                                         int t0)
@@ -253,14 +290,14 @@ __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1
     const int ga = max(q.gA, tg0), gb = min(q.gB, tg1);
     if (ga > gb) return;  // warp-uniform
     const int kfc = lane - q.c;
-    sweep<kBandGH1>(q, q.gA, q.L2 - 1, ga, gb, tg0, base, kfc, lane);
-    sweep<kBandGH2>(q, q.L2, q.L4 - 1, ga, gb, tg0, base, kfc, lane);
-    sweep<kBandGH4>(q, q.L4, q.Lc - 1, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH1, PEEL>(q, q.gA, q.L2 - 1, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH2, PEEL>(q, q.L2, q.L4 - 1, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH4, PEEL>(q, q.L4, q.Lc - 1, ga, gb, tg0, base, kfc, lane);
     if (q.Lc <= q.Rc)
         sweep_core(q, slot, q.Lc, q.Rc, ga, gb, tg0, base, kfc, lane, queue, qn, S, warp, t0);
-    sweep<kBandGH4>(q, q.Rc + 1, q.R4, ga, gb, tg0, base, kfc, lane);
-    sweep<kBandGH2>(q, q.R4 + 1, q.R2, ga, gb, tg0, base, kfc, lane);
-    sweep<kBandGH1>(q, q.R2 + 1, q.gB, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH4, PEEL>(q, q.Rc + 1, q.R4, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH2, PEEL>(q, q.R4 + 1, q.R2, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH1, PEEL>(q, q.R2 + 1, q.gB, ga, gb, tg0, base, kfc, lane);
 }
 
 __device__ __forceinline__ void fold(Smem &S, int tid)
@@ -279,6 +316,7 @@ __device__ __forceinline__ void fold(Smem &S, int tid)
     }
 }
 
+template <bool PEEL>
 __global__ void __launch_bounds__(NT, 3)
     k_gather_f32(const Prob *__restrict__ probs, GridD g, int64_t ntiles, int64_t m,
                  const int64_t *__restrict__ item_off, const int64_t *__restrict__ tile_lb,
@@ -345,7 +383,7 @@ __global__ void __launch_bounds__(NT, 3)
                 // a register copy: the record must not be re-read from shared
                 // memory after every store into the tile copy
                 const Rec q = S.rec[warp][j];
-                do_line(q, j, tg0, tg1, accb, lane, queue, qn, S, warp, t0);
+                do_line<PEEL>(q, j, tg0, tg1, accb, lane, queue, qn, S, warp, t0);
             }
             drain_rest(queue, qn, S, warp, lane, t0);
             if (++rounds == FLUSH_ROUNDS) {
@@ -372,26 +410,43 @@ int gather_f32_tile_bins() { return f32g::TILE; }
 
 size_t gather_f32_smem() { return sizeof(f32g::Smem); }
 
+// Lines at least this many bins wide take the peeled sweeps.
+constexpr double kPeelBins = 1024.0;
+
+template <bool PEEL>
+static int launch_variant(const Prob *probs_d, const GridD &g, int64_t ntiles, int64_t m,
+                          const int64_t *item_off, const int64_t *tile_lb,
+                          const int64_t *tile_le, int lmax, unsigned long long *counter,
+                          cudaStream_t st, int num_sms)
+{
+    static bool configured = false;
+    static int per_sm = 0;
+    cudaError_t e;
+    if (!configured) {
+        e = cudaFuncSetAttribute(f32g::k_gather_f32<PEEL>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(f32g::Smem));
+        if (e) return fail_cuda(e);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32g::k_gather_f32<PEEL>,
+                                                          f32g::NT, sizeof(f32g::Smem));
+        if (e || per_sm < 1) per_sm = 1;
+        configured = true;
+    }
+    f32g::k_gather_f32<PEEL><<<num_sms * per_sm, f32g::NT, sizeof(f32g::Smem), st>>>(
+        probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter);
+    e = cudaGetLastError();
+    return e ? fail_cuda(e) : HK_OK;
+}
+
 int gather_f32_launch(const Prob *probs_d, const GridD &g, int64_t ntiles, int64_t m,
                       const int64_t *item_off, const int64_t *tile_lb, const int64_t *tile_le,
                       int lmax, unsigned long long *counter, cudaStream_t st, int num_sms)
 {
-    static bool configured = false;
-    cudaError_t e;
-    if (!configured) {
-        e = cudaFuncSetAttribute(f32g::k_gather_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(f32g::Smem));
-        if (e) return fail_cuda(e);
-        configured = true;
-    }
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32g::k_gather_f32, f32g::NT,
-                                                      sizeof(f32g::Smem));
-    if (e || per_sm < 1) per_sm = 1;
-    f32g::k_gather_f32<<<num_sms * per_sm, f32g::NT, sizeof(f32g::Smem), st>>>(
-        probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter);
-    e = cudaGetLastError();
-    return e ? fail_cuda(e) : HK_OK;
+    const bool wide = g.W <= 0.0 || 2.0 * g.W + 1.0 >= kPeelBins;
+    return wide ? launch_variant<true>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
+                                       counter, st, num_sms)
+                : launch_variant<false>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
+                                        counter, st, num_sms);
 }
 
 }  // namespace hk

@@ -84,6 +84,17 @@ template <typename R> __device__ __forceinline__ R gh4_F(R X, R Y, R r2)
     return (wa * (r2 + ta) * d2 + wb * (r2 + tb) * d1) / (d1 * d2);
 }
 
+// 1/a from the hardware reciprocal alone (PTX rcp.approx.ftz.f32: at most
+// 1 ulp, subnormal arguments and results flushed to zero, so no fix-up path).
+// Every float sum here is scaled so that its peak is near 1: a term that
+// flushes lies below 2^-126 of the peak.
+__device__ __forceinline__ float rcp_ftz(float a)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
 template <typename R> struct Math;
 template <> struct Math<float> {
     static __device__ __forceinline__ float exp_(float a) { return expf(a); }
@@ -91,7 +102,7 @@ template <> struct Math<float> {
     static __device__ __forceinline__ void sincos_(float a, float *s, float *c) { sincosf(a, s, c); }
     static __device__ __forceinline__ void sincospi_(float a, float *s, float *c) { sincospif(a, s, c); }
     static __device__ __forceinline__ float floor_(float a) { return floorf(a); }
-    static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float div_(float a, float b) { return a * rcp_ftz(b); }
 };
 template <> struct Math<double> {
     static __device__ __forceinline__ double exp_(double a) { return exp(a); }
