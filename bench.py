@@ -29,14 +29,17 @@ sys.path.insert(0, ROOT)
 METRIC = "lines/s and Voigt evals/s on 1 GB300 (FP32-comp vs FP64 GPU) at stated σ error"
 
 # Cost model: FP32 flops per (line, bin) pair in each Faddeeva band of the
-# kernel (FMA = 2 flops; reciprocals, exp and sincos counted as 1 each):
-# shared x, x^2, r^2 and accumulate = 6; band formulas add 2 / 8 / 13 / 19
-# and ~194 for the trapezoid core.  Band counts come from hk_count_pairs.
-FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 19, "gh4": 25, "core": 200}
+# FP32-compensated kernel (FMA = 2 flops; reciprocals, exp and sincos counted
+# as 1 each): shared x, x^2, r^2 and accumulate = 6; band formulas add 2 (one
+# node, r2 >= 1.5e6), 8 (two nodes, r2 >= 2500), 19 (four nodes, r2 >= 64)
+# and ~194 for the trapezoid core (r2 < 64).  hk_count_pairs splits the
+# four-node range at r2 = 200 (the FP64 kernel's three-node band): both parts
+# are four-node work here.
+FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 25, "gh4": 25, "core": 200}
 # DRAM bytes per line of one k_gather_f32 launch, from the ncu capture in
-# profiles/k_gather_f32_config1-1e7-lines.md (248.1 MB for 1e7 lines; traffic
-# grows with the line count).  Set to None when the kernel changes.
-GATHER_DRAM_BYTES_PER_LINE = 24.81
+# profiles/k_gather_f32_config1-1e7-lines.md (traffic grows with the line
+# count).  None until the current kernel has been captured.
+GATHER_DRAM_BYTES_PER_LINE = None
 FP32_LANES_PER_SM = 128
 
 
