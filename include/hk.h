@@ -260,7 +260,8 @@ int hk_tuning(int precision, int *lmax);
 
 /* Instrumentation (no counterpart in the paper).  Counts the (line, bin)
  * pairs the cut admits for this problem: counts[0] = total (the algorithmic
- * Voigt-evaluation count, decided by the same FP64 predicate as the sum),
+ * Voigt-evaluation count, from the same cut bounds as the FP32 sum, which
+ * equal those of the FP64 predicate |(i - i0) - r| <= W),
  * counts[1..5] = pairs whose r2 = x^2 + y^2 falls in the Faddeeva bands
  * r2 >= 1.5e6, [2500, 1.5e6), [200, 2500), [64, 200), < 64 (band edges
  * decided in FP64, so a few pairs at an edge may differ from the kernel's

@@ -180,6 +180,18 @@ static int check_opts(const hk_opts *o)
     return HK_OK;
 }
 
+// The FP32 fast path of the cut bounds: W = Wi + Wf for 0 < W < 2^30.
+static void set_cut_split(GridD *d)
+{
+    if (d->W > 0.0 && d->W < 1073741824.0) {
+        d->Wi = (int)std::floor(d->W);
+        d->Wf = (float)(d->W - (double)d->Wi);
+    } else {
+        d->Wi = -1;
+        d->Wf = 0.0f;
+    }
+}
+
 static GridD make_grid(const hk_grid *g, const hk_opts *o)
 {
     GridD d;
@@ -191,6 +203,7 @@ static GridD make_grid(const hk_grid *g, const hk_opts *o)
     d.cut = nocut ? 0.0 : o->cut;
     d.W = (d.cut > 0.0) ? d.cut * d.inv_dnu : 0.0;
     if (d.cut <= 0.0) d.cut = 0.0;
+    set_cut_split(&d);
     return d;
 }
 
@@ -203,7 +216,23 @@ static GridD make_grid_cut(const hk_grid *g, double cut)
     d.nbins = g->nbins;
     d.cut = cut > 0.0 ? cut : 0.0;
     d.W = cut > 0.0 ? cut * d.inv_dnu : 0.0;
+    set_cut_split(&d);
     return d;
+}
+
+// Float copies of a problem's scalars (the FP32 strength uses only these).
+static void set_f32_scalars(Prob *p)
+{
+    p->qratio_f = (float)p->qratio;
+    p->c2T_f = (float)p->c2T;
+    p->c2Tref_f = (float)p->c2Tref;
+    p->mass_scale_f = (float)p->mass_scale;
+    p->aD_coef_f = (float)p->aD_coef;
+    p->log2_tratio_f = (float)p->log2_tratio;
+    p->press_f = (float)p->press;
+    p->nat_coef_f = (float)p->nat_coef;
+    p->K2_hi = (float)p->K2;
+    p->K2_lo = (float)(p->K2 - (double)p->K2_hi);
 }
 
 // FP64 scalars of one (species, T, P) problem.
@@ -238,6 +267,7 @@ static Prob make_prob(const hk_lines *L, const hk_state *s, const hk_opts *o)
     p.press = s->P / o->P_ref;
     p.inv_Pref = 1.0 / o->P_ref;
     p.nat_coef = 1.0 / (4.0 * kPI * kC);
+    set_f32_scalars(&p);
     return p;
 }
 

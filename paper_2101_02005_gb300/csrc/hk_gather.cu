@@ -387,15 +387,17 @@ __global__ void k_count_pairs(Prob p, GridD g, unsigned long long *counts)
     unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < p.n;
          l += (int64_t)gridDim.x * blockDim.x) {
-        int i0, lo, hi;
-        double r;
-        if (!line_geometry(p.nu0[l], g, &i0, &r, &lo, &hi)) continue;
+        // the FP32 kernels' geometry (its pair total must equal the oracle's)
+        int cb, lo, hi;
+        float rnf;
+        if (!line_geometry_f32(p.nu0[l], g, &cb, &rnf, &lo, &hi)) continue;
+        const double r = (double)rnf;
         double S, aDinv, y;
         line_strength_f64(p, l, &S, &aDinv, &y);
         double b = g.dnu * aDinv;
-        double klo = (double)(lo - i0), khi = (double)(hi - i0);
+        double klo = (double)(lo - cb), khi = (double)(hi - cb);
         c[0] += (unsigned long long)(hi - lo + 1);
-        // pairs with r2 < R2: |k - r| < sqrt(R2 - y^2) / b
+        // pairs with r2 < R2: |k - rn| < sqrt(R2 - y^2) / b, k = i - cb
         const double R2[4] = {1.5e6, 2500.0, 200.0, 64.0};
         unsigned long long inside[4];
         for (int t = 0; t < 4; ++t) {

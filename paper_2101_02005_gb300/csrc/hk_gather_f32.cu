@@ -94,17 +94,13 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
                                          Rec *out)
 {
     Rec q;
-    const double nu0 = pr.nu0[l];
-    int i0, lo, hi;
-    double r;
-    bool any = line_geometry(nu0, g, &i0, &r, &lo, &hi);
-    int c;
-    double rn;
-    nearest_bin(i0, r, &c, &rn);
+    int c, lo, hi;
+    float rn;
+    const bool any = line_geometry_f32(pr.nu0[l], g, &c, &rn, &lo, &hi);
     q.c = c;
     q.lo = lo;
     q.hi = hi;
-    q.rn = (float)rn;
+    q.rn = rn;
     float aDinv, y, sv;
     if (!any) {
         aDinv = 1.0f;

@@ -247,6 +247,10 @@ struct Prob {
     double press;               // P / P_ref
     double inv_Pref;            // 1 / P_ref
     double nat_coef;            // 1 / (4 pi c)
+    // the same scalars rounded to float (set with them on the host), for the
+    // FP32 strength; K2 as a float pair K2_hi + K2_lo (about 48 bits)
+    float qratio_f, c2T_f, c2Tref_f, mass_scale_f, aD_coef_f, log2_tratio_f, press_f,
+        nat_coef_f, K2_hi, K2_lo;
     // outputs
     double *acc;                // [nbins] FP64 accumulator (or the FP64 output itself)
     int *scale_exp;             // device int: sigma in acc is scaled by 2^-scale (FP32C)
@@ -262,6 +266,8 @@ struct GridD {
     double W;                   // cut / dnu (as cut * inv_dnu); <= 0: no cut
     double cut;
     int64_t nbins;
+    int Wi;                     // floor(W) for 0 < W < 2^30, else -1 (no fast cut path)
+    float Wf;                   // W - Wi rounded to float
 };
 
 // Per-line kernel parameters, as staged in shared memory.
@@ -321,6 +327,65 @@ __device__ __forceinline__ bool line_geometry(double nu0, const GridD &g, int *i
     return true;
 }
 
+// Bin geometry for the FP32 kernels, with as little FP64 arithmetic as the
+// exact cut decision allows (FP64 throughput is a small fraction of FP32).
+// u, i0 = floor(u) and r = u - i0 are the FP64 values of line_geometry.  The
+// bounds kh = max k with |k - r| <= W and kl = min such k (k = i - i0) are
+// floor(r + W) and ceil(r - W) of the exact reals unless r +- W lies within
+// about ulp(W) of an integer (the rounding of k - r in the predicate), so with
+// W = Wi + Wf they come from FP32 sums rf +- Wf (error below 3e-7) whenever
+// those lie more than 1e-5 from an integer; otherwise (and for W >= 2^30)
+// from line_geometry's exact FP64 walk.  Also returns the nearest bin c and
+// the offset rn in [-1/2, 1/2] (see nearest_bin) as a float.
+__device__ __forceinline__ bool line_geometry_f32(double nu0, const GridD &g, int *c_out,
+                                                  float *rn_out, int *lo_out, int *hi_out)
+{
+    const double u = __dmul_rn(__dsub_rn(nu0, g.nu_min), g.inv_dnu);
+    const double f = floor(u);
+    const double r = __dsub_rn(u, f);
+    const float rf = (float)r;
+    long long lo, hi;
+    const long long i0 = (long long)f;
+    bool exact = true;
+    if (g.W <= 0.0) {
+        lo = 0;
+        hi = g.nbins - 1;
+        exact = false;
+    } else if (g.Wi >= 0) {
+        const float sh = rf + g.Wf, sl = rf - g.Wf;
+        const float th = sh - rintf(sh), tl = sl - rintf(sl);
+        if (fabsf(th) > 1e-5f && fabsf(tl) > 1e-5f) {
+            hi = i0 + g.Wi + (long long)floorf(sh);
+            lo = i0 - g.Wi + (long long)ceilf(sl);
+            exact = false;
+        }
+    }
+    if (exact) {
+        int i0e, loe, hie;
+        double re;
+        const bool any = line_geometry(nu0, g, &i0e, &re, &loe, &hie);
+        lo = any ? loe : 1;
+        hi = any ? hie : 0;
+    } else {
+        if (lo < 0) lo = 0;
+        if (hi > g.nbins - 1) hi = g.nbins - 1;
+        if (!(nu0 > 0.0) || i0 < -2147483647LL || i0 > 2147483647LL) hi = lo - 1;
+    }
+    if (hi < lo) {
+        *c_out = 0;
+        *rn_out = 0.0f;
+        *lo_out = 0x3fffffff;
+        *hi_out = -0x3fffffff;
+        return false;
+    }
+    const bool up = rf >= 0.5f;   // either choice is a valid nearest-bin split
+    *c_out = (int)i0 + (up ? 1 : 0);
+    *rn_out = (float)(up ? r - 1.0 : r);
+    *lo_out = (int)lo;
+    *hi_out = (int)hi;
+    return true;
+}
+
 // Offset of bin i from the line centre in bins, as (i - c) - rn with the
 // NEAREST bin c and rn in [-1/2, 1/2]: for |i - c| >= 1 the float subtraction
 // is well conditioned and for i = c the offset is -rn itself, so a bin that
@@ -342,23 +407,26 @@ __device__ __forceinline__ void nearest_bin(int i0, double r, int *c, double *rn
 __device__ __forceinline__ void line_strength_f32(const Prob &p, int64_t l, float *P_out,
                                                   int *e2_out, float *aDinv_out, float *y_out)
 {
-    double nu0 = p.nu0[l];
-    float nu0f = (float)nu0;
-    float aDinv = (float)p.aD_coef / nu0f;
-    float nat = p.A ? p.A[l] * (float)p.nat_coef : 0.0f;
-    float GL = nat + p.gamma[l] * exp2f(p.n_T[l] * (float)p.log2_tratio) * (float)p.press;
-    double L = (double)p.E_low[l] * p.K2;   // log2 of the Boltzmann factor
-    double nL = rint(L);
-    float bz = exp2f((float)(L - nL));
+    const float nu0f = (float)p.nu0[l];
+    float aDinv = p.aD_coef_f / nu0f;
+    float nat = p.A ? p.A[l] * p.nat_coef_f : 0.0f;
+    float GL = nat + p.gamma[l] * exp2f(p.n_T[l] * p.log2_tratio_f) * p.press_f;
+    // log2 of the Boltzmann factor, E'' K2, as a float pair Lh + Ll: E'' is a
+    // float, so E'' K2_hi has the exact error term fma(E'', K2_hi, -Lh)
+    const float E = p.E_low[l];
+    const float Lh = E * p.K2_hi;
+    const float Ll = fmaf(E, p.K2_lo, fmaf(E, p.K2_hi, -Lh));
+    const float nL = rintf(Lh);
+    float bz = exp2f((Lh - nL) + Ll);   // Lh - nL is exact
     float P;
     if (p.s_mode == 0) {
-        float stim = expm1f(-(float)p.c2T * nu0f) / expm1f(-(float)p.c2Tref * nu0f);
-        P = p.S_ref[l] * (float)p.qratio * bz * stim;
+        float stim = expm1f(-p.c2T_f * nu0f) / expm1f(-p.c2Tref_f * nu0f);
+        P = p.S_ref[l] * p.qratio_f * bz * stim;
     } else {
-        float stim = -expm1f(-(float)p.c2T * nu0f);
-        P = p.A[l] * p.g_up[l] * (float)p.qratio / (nu0f * nu0f) * bz * stim;
+        float stim = -expm1f(-p.c2T_f * nu0f);
+        P = p.A[l] * p.g_up[l] * p.qratio_f / (nu0f * nu0f) * bz * stim;
     }
-    P = P * (aDinv * (float)kInvSqrtPi) * (float)p.mass_scale;
+    P = P * (aDinv * (float)kInvSqrtPi) * p.mass_scale_f;
     *P_out = P;
     *e2_out = (int)nL;
     *aDinv_out = aDinv;

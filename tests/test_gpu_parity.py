@@ -77,6 +77,37 @@ def test_ragged_grid_off_grid_lines_and_cut_variants(hk, prec):
         assert np.array_equal(ref == 0, got == 0)
 
 
+def test_cut_ties_match_oracle(hk):
+    """Line centres on and a hair off bin centres and half-bins, with cuts
+    whose W = cut / dnu is an integer, a hair above one, and fractional: the
+    cut bounds (FP32 fast path with the exact FP64 walk near ties) give the
+    oracle's pair total exactly, the same zero pattern, and parity."""
+    deltas = [0.0, 1e-12, -1e-12, 1e-9, -1e-9, 2e-6, -2e-6, 9e-6, -9e-6, 0.5, 0.5 + 1e-9,
+              0.5 - 1e-9, 0.25, 0.999999, 1e-5, -1e-5]
+    for dnu, cut in [(0.1, 25.0), (0.1, 2.5), (0.01, 1.0), (0.1, 25.0 + 1e-10), (0.1, 0.35),
+                     (0.05, 0.125), (0.03, 0.3)]:
+        nbins = 1800
+        base = np.arange(40, nbins - 40, 97)
+        nu0 = np.sort(np.array([(i + d) * dnu for i in base for d in deltas], dtype=np.float64))
+        n = nu0.size
+        rng = np.random.default_rng(int(cut * 1000) + int(1 / dnu))
+        L = synth.LineList(nu0, (10 ** rng.uniform(-22, -20, n)).astype(np.float32),
+                           rng.exponential(1000, n).astype(np.float32),
+                           rng.uniform(0.01, 0.1, n).astype(np.float32),
+                           rng.uniform(0.3, 0.8, n).astype(np.float32), 18.0)
+        grid = synth.Grid(0.0, dnu, nbins)
+        D = hk.DeviceLines.from_host(L)
+        counts = hk.hk_count_pairs(D, hk.make_grid(*grid.astuple()),
+                                   hk.make_state(900.0, 0.5, float(Q(900.0))),
+                                   hk.make_opts(QREF, cut))
+        assert counts[0] == oracle.count_pairs(L.nu0, *grid.astuple(), cut), (dnu, cut)
+        ref = oracle_sigma(L, grid, 900.0, 0.5, cut)
+        for prec in (0, 1):
+            got = gpu_sigma(hk, L, grid, 900.0, 0.5, cut, prec)
+            assert_sigma_close(got, ref, f"ties dnu={dnu} cut={cut} prec={prec}")
+            assert np.array_equal(ref == 0, got == 0), (dnu, cut, prec)
+
+
 def test_zero_lines_and_single_line(hk):
     L0 = synth.make_lines(0, 0, 10, 1, 18.0)
     grid = synth.Grid(0.0, 0.01, 1000)
