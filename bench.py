@@ -37,9 +37,9 @@ METRIC = "lines/s and Voigt evals/s on 1 GB300 (FP32-comp vs FP64 GPU) at stated
 # are four-node work here.
 FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 25, "gh4": 25, "core": 200}
 # DRAM bytes per line of one k_gather_f32 launch, from the ncu capture in
-# profiles/k_gather_f32_config1-1e7-lines.md (traffic grows with the line
-# count).  None until the current kernel has been captured.
-GATHER_DRAM_BYTES_PER_LINE = None
+# profiles/k_gather_f32_config1-1e7-lines.md (277.9 MB for 1e7 lines; traffic
+# grows with the line count).  Set to None when the kernel changes.
+GATHER_DRAM_BYTES_PER_LINE = 27.79
 FP32_LANES_PER_SM = 128
 
 
@@ -296,7 +296,7 @@ def main():
     achieved = flops_step / (g_ms / 1e3) / 1e12
     traffic = (GATHER_DRAM_BYTES_PER_LINE * L.n
                if GATHER_DRAM_BYTES_PER_LINE and args.config == 1 else None)
-    roofline = {"bound": "alu", "kernel": "k_gather_f32", "achieved": achieved,
+    roofline = {"bound": "alu", "kernel": "k_gather_f32<false>" if 2 * w.cut / w.grid.dnu + 1 < 1024 else "k_gather_f32<true>", "achieved": achieved,
                 "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
                 "traffic": traffic, "algorithmic_bytes": 24 * L.n, "gather_ms_per_launch": g_ms,
                 "gather_share_of_step": g_ms / ms_step if ms_step else None,
