@@ -175,6 +175,33 @@ int hk_voigt_accumulate(const double *nu0, const double *S, const float *alphaD_
 int hk_cross_section(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
                      const hk_opts *opts, void *sigma_out, void *stream);
 
+/* hk_cross_section for a line list in HOST memory, streamed to the GPU in
+ * blocks whose copies overlap the sums of the previous block (Sect. 2.3;
+ * Sect. 2.4.1, asynchronous interleaved copies of line-list blocks;
+ * Sect. 2.4.6 and its workflow figure, copies "C" hidden behind the
+ * kernels).  Blocks grow from chunk_lines/8 to chunk_lines lines (0: 2^23,
+ * two device buffers of 200 MB for five fields); each is copied on an
+ * internal copy stream into one of two device buffers, then summed exactly
+ * as hk_cross_section sums a device-resident list (its own strength, FP32
+ * scale and tile schedule) into an FP64 partial sigma.  Even blocks run on
+ * `stream`, odd ones on an internal second stream (so one block's work fills
+ * the SMs the previous block's launch leaves idle at its end); `stream` then
+ * adds the two partial sums, converts to the output type and copies the
+ * result to sigma_out.  The sum over blocks is a sum over lines, so the
+ * result equals hk_cross_section's up to the FP32 rounding of the per-block
+ * tile sums.
+ * lines: the hk_lines fields are HOST pointers (page-locked memory gives
+ * full copy speed and overlap; pageable memory works, slower); the list may
+ * be unsorted (each block is then sorted on the GPU).  sigma_out: HOST or
+ * DEVICE float[nbins] (HK_FP32C) or double[nbins] (HK_FP64, or
+ * HK_SIGMA_F64), overwritten.  Everything is enqueued on `stream`: the
+ * host buffers must stay valid, and sigma_out is complete, once `stream`
+ * has synchronised.  Calls on one device share the library's scratch pool
+ * and copy stream and must not overlap. */
+int hk_cross_section_host(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
+                          const hk_opts *opts, void *sigma_out, int64_t chunk_lines,
+                          void *stream);
+
 /* hk_cross_section for callers that must not allocate device memory.  The
  * paper has no counterpart; this is a service of the library.
  *

@@ -573,6 +573,165 @@ int hk_cross_section(const hk_lines *lines, const hk_grid *grid, const hk_state 
                               t.lmax);
 }
 
+// ---- hk_cross_section_host: host line list streamed in blocks ----------------
+// Per device: a copy stream, a second compute stream and five events.  Blocks
+// alternate between buffer/stream pair 0 (the caller's stream) and pair 1
+// (the second compute stream), each pair with its own gather workspace and
+// FP64 partial sigma, so one block's kernels can fill the SMs that the
+// previous block's persistent launch leaves idle at its end.  `start` orders
+// all of it after earlier work on the caller's stream (which may still read
+// the pool); copied[b] / done[b] hand buffer b between the copy stream and
+// compute stream b; the caller's stream finally waits for done[1] and adds
+// the two partial sums.
+struct CopyCtx {
+    cudaStream_t cs = nullptr, st2 = nullptr;
+    cudaEvent_t start = nullptr, copied[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr};
+};
+static std::mutex g_copy_mu;
+static std::map<int, CopyCtx> g_copy;
+
+static int copy_ctx(CopyCtx **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return fail_cuda(e);
+    std::lock_guard<std::mutex> lk(g_copy_mu);
+    auto it = g_copy.find(dev);
+    if (it != g_copy.end()) {
+        *out = &it->second;
+        return HK_OK;
+    }
+    CopyCtx c;
+    e = cudaStreamCreateWithFlags(&c.cs, cudaStreamNonBlocking);
+    if (!e) e = cudaStreamCreateWithFlags(&c.st2, cudaStreamNonBlocking);
+    cudaEvent_t *evs[5] = {&c.start, &c.copied[0], &c.copied[1], &c.done[0], &c.done[1]};
+    for (int i = 0; i < 5 && !e; ++i) e = cudaEventCreateWithFlags(evs[i], cudaEventDisableTiming);
+    if (e) return fail_cuda(e);
+    *out = &(g_copy[dev] = c);
+    return HK_OK;
+}
+
+// out = a (+ b), as double (o64) or float (o32, with the overflow flag).
+__global__ void k_combine(const double *__restrict__ a, const double *__restrict__ b,
+                          double *o64, float *o32, int64_t n, unsigned *status)
+{
+    bool over = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = b ? a[i] + b[i] : a[i];
+        if (o64) {
+            o64[i] = v;
+        } else {
+            const float f = (float)v;
+            over |= isinf(f) && !isinf(v);
+            o32[i] = f;
+        }
+    }
+    if (over) atomicOr(status, kStatusRange);
+}
+
+int hk_cross_section_host(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
+                          const hk_opts *opts, void *sigma_out, int64_t chunk_lines,
+                          void *stream)
+{
+    int rc;
+    if ((rc = check_lines(lines, true)) || (rc = check_grid(grid)) || (rc = check_state(state)) ||
+        (rc = check_opts(opts)))
+        return rc;
+    if (!sigma_out || chunk_lines < 0) return HK_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int prec = opts->precision;
+    const int out_f64 = (prec == HK_FP64 || (opts->flags & HK_SIGMA_F64)) ? 1 : 0;
+    const int64_t n = lines->n, nbins = grid->nbins;
+    const int64_t C = std::max<int64_t>(1, std::min<int64_t>(chunk_lines > 0 ? chunk_lines
+                                                                             : (int64_t)1 << 23,
+                                                             std::max<int64_t>(n, 1)));
+    // float fields present (S_ref, E_low, gamma_ref, n_T, A, g_up)
+    const float *hf[6] = {lines->S_ref, lines->E_low, lines->gamma_ref, lines->n_T, lines->A,
+                          lines->g_up};
+    Tune t = get_tune(prec);
+    const GridD g = make_grid(grid, opts);
+    const size_t need_g = al(gather_workspace(1, nbins, prec, t.bpt));
+    size_t cub_b = 0;
+    const size_t sort_need = lines->sorted ? 0 : al(sort_bytes(C, &cub_b));
+    size_t buf = al((size_t)C * 8);
+    for (int f = 0; f < 6; ++f)
+        if (hf[f]) buf += al((size_t)C * 4);
+    const size_t sig_b = al((size_t)nbins * 8);
+    const size_t out_b = out_f64 ? sig_b : al((size_t)nbins * 4);
+    const size_t per_pair = need_g + sort_need + buf + sig_b;
+    char *ws;
+    if ((rc = pool_get(2 * per_pair + out_b, &ws))) return rc;
+    char *ws_g[2], *ws_sort[2], *bufs[2];
+    double *sig[2];
+    for (int b = 0; b < 2; ++b) {
+        char *base = ws + b * per_pair;
+        ws_g[b] = base;
+        ws_sort[b] = base + need_g;
+        bufs[b] = base + need_g + sort_need;
+        sig[b] = (double *)(base + need_g + sort_need + buf);
+    }
+    char *outbuf = ws + 2 * per_pair;
+    unsigned *sw = status_word();
+    if (!sw) return HK_ENOMEM;
+    CopyCtx *cx;
+    if ((rc = copy_ctx(&cx))) return rc;
+    cudaStream_t cst[2] = {st, cx->st2};
+    cudaError_t e;
+    if ((e = cudaEventRecord(cx->start, st))) return fail_cuda(e);
+    if ((e = cudaStreamWaitEvent(cx->cs, cx->start, 0))) return fail_cuda(e);
+    if ((e = cudaStreamWaitEvent(cx->st2, cx->start, 0))) return fail_cuda(e);
+    const int nsms = num_sms();
+    // blocks grow from C/8 to C so the first copy, which nothing hides, is short
+    int64_t nblk = 0;
+    for (int64_t off = 0, i = 0; off < n; ++i, ++nblk) {
+        const int b = (int)(i & 1);
+        const int64_t cap = i < 3 ? std::max<int64_t>(1, C >> (3 - i)) : C;
+        const int64_t cnt = std::min(cap, n - off);
+        if (i >= 2 && (e = cudaStreamWaitEvent(cx->cs, cx->done[b], 0))) return fail_cuda(e);
+        hk_lines L = *lines;
+        L.n = cnt;
+        char *cur = bufs[b];
+        L.nu0 = (const double *)cur;
+        if ((e = cudaMemcpyAsync(cur, lines->nu0 + off, sizeof(double) * cnt, cudaMemcpyDefault,
+                                 cx->cs)))
+            return fail_cuda(e);
+        cur += al((size_t)C * 8);
+        const float **lf[6] = {&L.S_ref, &L.E_low, &L.gamma_ref, &L.n_T, &L.A, &L.g_up};
+        for (int f = 0; f < 6; ++f) {
+            if (!hf[f]) continue;
+            *lf[f] = (const float *)cur;
+            if ((e = cudaMemcpyAsync(cur, hf[f] + off, sizeof(float) * cnt, cudaMemcpyDefault,
+                                     cx->cs)))
+                return fail_cuda(e);
+            cur += al((size_t)C * 4);
+        }
+        if ((e = cudaEventRecord(cx->copied[b], cx->cs))) return fail_cuda(e);
+        if ((e = cudaStreamWaitEvent(cst[b], cx->copied[b], 0))) return fail_cuda(e);
+        hk_lines Ls = L;
+        if (!lines->sorted) {
+            int64_t *perm;
+            if ((rc = sort_lines(&L, ws_sort[b], &Ls, &perm, cst[b]))) return rc;
+        }
+        Prob p = make_prob(&Ls, state, opts);
+        if ((rc = gather_run(&p, 1, g, prec, t.bpt, t.lmax, sig[b], 1, i >= 2 ? 1 : 0, ws_g[b],
+                             need_g, sw, cst[b], nsms)))
+            return rc;
+        if ((e = cudaEventRecord(cx->done[b], cst[b]))) return fail_cuda(e);
+        off += cnt;
+    }
+    if (nblk == 0 && (e = cudaMemsetAsync(sig[0], 0, sizeof(double) * (size_t)nbins, st)))
+        return fail_cuda(e);
+    if (nblk >= 2 && (e = cudaStreamWaitEvent(st, cx->done[1], 0))) return fail_cuda(e);
+    k_combine<<<nsms * 4, 256, 0, st>>>(sig[0], nblk >= 2 ? sig[1] : nullptr,
+                                        out_f64 ? (double *)outbuf : nullptr,
+                                        out_f64 ? nullptr : (float *)outbuf, nbins, sw);
+    if ((e = cudaGetLastError())) return fail_cuda(e);
+    const size_t bytes = (out_f64 ? sizeof(double) : sizeof(float)) * (size_t)nbins;
+    if ((e = cudaMemcpyAsync(sigma_out, outbuf, bytes, cudaMemcpyDefault, st))) return fail_cuda(e);
+    return HK_OK;
+}
+
 // ---- hk_cross_section_noalloc: scratch in a fixed device array ---------------
 // The array lives in device memory of every GPU that loads the library.  Host
 // code must never hand the symbol itself to a kernel (on the host it names a

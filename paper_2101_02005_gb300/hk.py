@@ -27,7 +27,7 @@ EXPORTS = ["hk_line_strength", "hk_widths", "hk_voigt_accumulate", "hk_cross_sec
            "hk_cross_section_batched", "hk_cross_section_backward", "hk_workspace_size",
            "hk_autotune", "hk_sync_status", "hk_release", "hk_strerror", "hk_last_cuda_error",
            "hk_constants", "hk_version", "hk_count_pairs", "hk_profile",
-           "hk_cross_section_noalloc", "hk_tuning"]
+           "hk_cross_section_noalloc", "hk_tuning", "hk_cross_section_host"]
 
 
 class hk_lines(ctypes.Structure):
@@ -99,6 +99,8 @@ def lib():
     L.hk_tuning.argtypes = [ctypes.c_int, P(ctypes.c_int)]
     L.hk_cross_section_noalloc.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts),
                                            vp, vp]
+    L.hk_cross_section_host.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts), vp,
+                                        ctypes.c_int64, vp]
     _lib = L
     return L
 
@@ -159,6 +161,23 @@ class DeviceLines:
                            t(L.E_low, torch.float32), t(L.gamma_ref, torch.float32),
                            t(L.n_T, torch.float32), L.mass_amu, A=t(L.A, torch.float32),
                            g_up=t(L.g_up, torch.float32), s_mode=L.s_mode, sorted=L.sorted)
+
+
+class HostLines(DeviceLines):
+    """A line list in host memory (page-locked by default), for
+    hk_cross_section_host; the same fields as DeviceLines, on the CPU."""
+
+    @staticmethod
+    def from_host(L, device="cpu", pin=True) -> "HostLines":
+        def t(a, dt):
+            if a is None:
+                return None
+            x = torch.from_numpy(a).to(dt).contiguous()
+            return x.pin_memory() if pin else x
+        return HostLines(t(L.nu0, torch.float64), t(L.S_ref, torch.float32),
+                         t(L.E_low, torch.float32), t(L.gamma_ref, torch.float32),
+                         t(L.n_T, torch.float32), L.mass_amu, A=t(L.A, torch.float32),
+                         g_up=t(L.g_up, torch.float32), s_mode=L.s_mode, sorted=L.sorted)
 
 
 def make_grid(nu_min, dnu, nbins) -> hk_grid:
@@ -223,6 +242,22 @@ def hk_cross_section(lines: DeviceLines, grid: hk_grid, state: hk_state, opts: h
     _check("hk_cross_section", lib().hk_cross_section(ctypes.byref(L), ctypes.byref(grid),
                                                       ctypes.byref(state), ctypes.byref(opts),
                                                       _ptr(sigma_out), _stream(stream)))
+    return sigma_out
+
+
+def hk_cross_section_host(lines: HostLines, grid: hk_grid, state: hk_state, opts: hk_opts,
+                          sigma_out=None, chunk_lines=0, stream=None):
+    """Cross section of a host-resident line list, streamed to the GPU in
+    blocks of chunk_lines (0: the library default).  sigma_out: a host
+    (page-locked by default) or device tensor; complete once the stream has
+    synchronised."""
+    if sigma_out is None:
+        sigma_out = torch.empty(grid.nbins, dtype=sigma_dtype(opts), pin_memory=True)
+    L = lines.struct()
+    _check("hk_cross_section_host",
+           lib().hk_cross_section_host(ctypes.byref(L), ctypes.byref(grid), ctypes.byref(state),
+                                       ctypes.byref(opts), _ptr(sigma_out), int(chunk_lines),
+                                       _stream(stream)))
     return sigma_out
 
 

@@ -108,6 +108,49 @@ def test_cut_ties_match_oracle(hk):
             assert np.array_equal(ref == 0, got == 0), (dnu, cut, prec)
 
 
+def test_host_streamed_matches_oracle(hk):
+    """hk_cross_section_host: the config-0 list in host memory, streamed in
+    ragged blocks (1e4 lines in blocks of 1500), against the oracle and the
+    device-resident call; FP64, unsorted and pageable inputs; empty list."""
+    w = synth.config(0)
+    L = w.species[0]
+    T, P = w.states()[0]
+    grid = hk.make_grid(*w.grid.astuple())
+    st = hk.make_state(T, P, float(Q(T)))
+    ref = oracle_sigma(L, w.grid, T, P, w.cut)
+    H = hk.HostLines.from_host(L)
+    o32 = hk.make_opts(QREF, w.cut)
+    got = hk.hk_cross_section_host(H, grid, st, o32, chunk_lines=1500)
+    hk.hk_sync_status()
+    assert got.dtype == torch.float32 and not got.is_cuda
+    assert_sigma_close(got.numpy(), ref, "host fp32c")
+    dev = hk.hk_cross_section(hk.DeviceLines.from_host(L), grid, st, o32)
+    hk.hk_sync_status()
+    e = sigma_errors(got.numpy(), dev.cpu().numpy())
+    assert e["max_bin"] <= 1e-6, e
+    for prec, flags in ((hk.HK_FP64, 0), (hk.HK_FP32C, hk.HK_SIGMA_F64)):
+        g64 = hk.hk_cross_section_host(H, grid, st, hk.make_opts(QREF, w.cut, prec, flags=flags),
+                                       chunk_lines=4096)
+        hk.hk_sync_status()
+        assert g64.dtype == torch.float64
+        assert_sigma_close(g64.numpy(), ref, f"host prec={prec}")
+    perm = np.random.default_rng(5).permutation(L.n)
+    U = L.subset(perm)
+    U.sorted = False
+    gu = hk.hk_cross_section_host(hk.HostLines.from_host(U, pin=False), grid, st,
+                                  hk.make_opts(QREF, w.cut, flags=hk.HK_SIGMA_F64),
+                                  chunk_lines=3000)
+    hk.hk_sync_status()
+    assert_sigma_close(gu.numpy(), ref, "host unsorted pageable")
+    gd = hk.hk_cross_section_host(H, grid, st, o32)          # default block size
+    hk.hk_sync_status()
+    assert_sigma_close(gd.numpy(), ref, "host default chunk")
+    E = hk.HostLines.from_host(synth.make_lines(0, 0, 10, 1, 18.0))
+    ge = hk.hk_cross_section_host(E, grid, st, o32)
+    hk.hk_sync_status()
+    assert np.all(ge.numpy() == 0)
+
+
 def test_zero_lines_and_single_line(hk):
     L0 = synth.make_lines(0, 0, 10, 1, 18.0)
     grid = synth.Grid(0.0, 0.01, 1000)
