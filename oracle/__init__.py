@@ -42,6 +42,14 @@ def lib():
         _lib.hko_sigma.argtypes = [i64, d, d, d, d, ctypes.c_int, ctypes.c_double,
                                    ctypes.c_double, i64, ctypes.c_double, i64, i64, d,
                                    ctypes.c_int]
+        _lib.hko_line_cuts.argtypes = [i64, d, d, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, d]
+        _lib.hko_count_pairs_percut.argtypes = [i64, d, d, ctypes.c_double, ctypes.c_double,
+                                                i64]
+        _lib.hko_count_pairs_percut.restype = i64
+        _lib.hko_sigma_ext.argtypes = [i64, d, d, d, d, d, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, i64, ctypes.c_double,
+                                       i64, i64, d, ctypes.c_int]
         _lib.hko_backward.argtypes = [i64, d, d, d, d, d, d] + [ctypes.c_double] * 10 + [
             i64, ctypes.c_double, d, d, d, d, d, ctypes.c_int]
     return _lib
@@ -143,29 +151,57 @@ def count_pairs(nu0, nu_min, dnu, nbins, cut):
     return int(lib().hko_count_pairs(nu0.size, _d(nu0), nu_min, dnu, nbins, cut))
 
 
+CUT_FIXED, CUT_NONE, CUT_DOPPLER, CUT_LORENTZ = 0, 1, 2, 3
+
+
+def line_cuts(nu0, gammaL, mode, factor, T, mass_amu):
+    """Per-line cutting lengths (Sect. 2.4.3 item 4): mode CUT_DOPPLER = factor
+    times Gamma_D = sqrt(ln 2) alpha_D (Eq. gammaD), CUT_LORENTZ = factor times
+    Gamma_L."""
+    nu0 = _f64(nu0)
+    n = nu0.size
+    GL = _f64(gammaL, n)
+    out = np.empty(n)
+    lib().hko_line_cuts(n, _d(nu0), _d(GL), int(mode), float(factor), float(T),
+                        float(mass_amu), _d(out))
+    return out
+
+
+def count_pairs_percut(nu0, cut_l, nu_min, dnu, nbins):
+    nu0 = _f64(nu0)
+    c = _f64(cut_l, nu0.size)
+    return int(lib().hko_count_pairs_percut(nu0.size, _d(nu0), _d(c), nu_min, dnu, nbins))
+
+
 def sigma(nu0, S, alphaD, gammaL, nu_min, dnu, nbins, cut, bin_lo=0, bin_hi=None,
-          sorted_nu0=False, nthreads=0):
-    """sigma_i for bins [bin_lo, bin_hi): the direct FP64 sum of S * Re w / (alpha_D sqrt(pi))."""
+          sorted_nu0=False, nthreads=0, cut_l=None, plinth=False):
+    """sigma_i for bins [bin_lo, bin_hi): the direct FP64 sum of S * Re w / (alpha_D sqrt(pi)).
+    cut_l: per-line cutting lengths (overrides `cut`); plinth: subtract each
+    line's value at its cutting length inside its cut (Sect. 2.1)."""
     nu0 = _f64(nu0)
     n = nu0.size
     S = _f64(S, n)
     aD = _f64(alphaD, n)
     GL = _f64(gammaL, n)
+    cl = _f64(cut_l, n)
     if bin_hi is None:
         bin_hi = nbins
     out = np.zeros(max(bin_hi - bin_lo, 0))
-    lib().hko_sigma(n, _d(nu0), _d(S), _d(aD), _d(GL), int(bool(sorted_nu0)), nu_min, dnu,
-                    nbins, cut, bin_lo, bin_hi, _d(out), int(nthreads))
+    lib().hko_sigma_ext(n, _d(nu0), _d(S), _d(aD), _d(GL), _d(cl) if cl is not None else None,
+                        int(bool(plinth)), int(bool(sorted_nu0)), nu_min, dnu, nbins, cut,
+                        bin_lo, bin_hi, _d(out), int(nthreads))
     return out
 
 
 def cross_section(lines, grid, state, cut, bin_lo=0, bin_hi=None, nthreads=0,
-                  T_ref=T_REF, P_ref=P_REF, per_gram=False):
+                  T_ref=T_REF, P_ref=P_REF, per_gram=False, cut_mode=CUT_FIXED, plinth=False):
     """Full path for one (T, P): S(T), widths, then the direct sum.
 
     ``lines``: mapping with nu0, E_low, gamma_ref, n_T and S_ref (s_mode 0) or
     A + g_up (s_mode 1), optional A for the natural term, mass_amu, s_mode,
     sorted.  ``grid``: (nu_min, dnu, nbins).  ``state``: (T, P, Q_T, Q_Tref).
+    cut_mode CUT_DOPPLER / CUT_LORENTZ: ``cut`` is the factor of the per-line
+    half width; CUT_NONE: no cut.  plinth: remove the plinth (Sect. 2.1).
     """
     nu_min, dnu, nbins = grid
     T, P, Q_T, Q_Tref = state[:4]
@@ -175,8 +211,14 @@ def cross_section(lines, grid, state, cut, bin_lo=0, bin_hi=None, nthreads=0,
                       s_mode=s_mode, T_ref=T_ref, per_gram=per_gram)
     aD, GL = widths(lines["nu0"], lines["gamma_ref"], lines["n_T"], T, P, lines["mass_amu"],
                     A=lines.get("A"), T_ref=T_ref, P_ref=P_ref)
+    cut_l = None
+    if cut_mode == CUT_NONE:
+        cut = 0.0
+    elif cut_mode in (CUT_DOPPLER, CUT_LORENTZ):
+        cut_l = line_cuts(lines["nu0"], GL, cut_mode, cut, T, lines["mass_amu"])
     return sigma(lines["nu0"], S, aD, GL, nu_min, dnu, nbins, cut, bin_lo, bin_hi,
-                 sorted_nu0=bool(lines.get("sorted", False)), nthreads=nthreads)
+                 sorted_nu0=bool(lines.get("sorted", False)), nthreads=nthreads, cut_l=cut_l,
+                 plinth=plinth)
 
 
 def backward(lines, grid, state, cut, grad_sigma, dL_dSref=None, dL_dgamma=None, nthreads=0,

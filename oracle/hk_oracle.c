@@ -249,24 +249,24 @@ static int in_cut(int64_t k, double r, double W)
 }
 
 /* Inclusive bin range [*lo, *hi] of a line clipped to [0, nbins); empty if
- * *lo > *hi.  The bounds come from the predicate itself: a first guess is
- * walked until in_cut changes, so every bin in the range satisfies in_cut and
- * its neighbours do not. */
-static void line_range(double nu0, double nu_min, double dnu, int64_t nbins, double cut,
-                       int64_t *lo, int64_t *hi)
+ * *lo > *hi.  nocut: every bin of the grid; else the bins with
+ * |(i - i0) - r| <= W, W = cut / dnu of this line (W >= 0).  The bounds come
+ * from the predicate itself: a first guess is walked until in_cut changes, so
+ * every bin in the range satisfies in_cut and its neighbours do not. */
+static void line_range_w(double nu0, double nu_min, double dnu, int64_t nbins, int nocut,
+                         double W, int64_t *lo, int64_t *hi)
 {
     if (!(nu0 > 0.0)) { /* no Doppler width (Eq. gammaD is proportional to nu0): ignored */
         *lo = 1;
         *hi = 0;
         return;
     }
-    if (cut <= 0.0) {
+    if (nocut) {
         *lo = 0;
         *hi = nbins - 1;
         return;
     }
     bin_pos p = line_pos(nu0, nu_min, dnu);
-    double W = cut * (1.0 / dnu);
     /* k offsets relative to i0 */
     int64_t a = (int64_t)floor(p.r - W) - 1;
     int64_t b = (int64_t)ceil(p.r + W) + 1;
@@ -287,12 +287,51 @@ static void line_range(double nu0, double nu_min, double dnu, int64_t nbins, dou
     *hi = H;
 }
 
+/* A fixed cutting length: cut <= 0 means no cut (the whole grid). */
+static void line_range(double nu0, double nu_min, double dnu, int64_t nbins, double cut,
+                       int64_t *lo, int64_t *hi)
+{
+    line_range_w(nu0, nu_min, dnu, nbins, !(cut > 0.0), cut * (1.0 / dnu), lo, hi);
+}
+
+/* Per-line cutting lengths of Sect. 2.4.3 item 4: mode 2 = factor times the
+ * Doppler half width Gamma_D = sqrt(ln 2) alpha_D (Eq. gammaD), mode 3 =
+ * factor times the Lorentz half width Gamma_L.  The Doppler form is evaluated
+ * as factor * (nu0 * K_D) with K_D = sqrt(ln 2) * sqrt(2 k_B T / m) / c (one
+ * constant per (T, species)), so that the cut decision is a fixed sequence of
+ * correctly rounded operations. */
+void hko_line_cuts(int64_t n, const double *nu0, const double *gammaL, int mode, double factor,
+                   double T, double mass_amu, double *cut_out)
+{
+    const double m_g = mass_amu * O_AMU;
+    const double K_D = sqrt(0.6931471805599453) * sqrt(2.0 * O_KB * T / m_g) / O_C;
+#pragma omp parallel for schedule(static)
+    for (int64_t l = 0; l < n; ++l)
+        cut_out[l] = mode == 2 ? factor * (nu0[l] * K_D) : factor * gammaL[l];
+}
+
 void hko_line_ranges(int64_t n, const double *nu0, double nu_min, double dnu, int64_t nbins,
                      double cut, int64_t *lo, int64_t *hi)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t l = 0; l < n; ++l)
         line_range(nu0[l], nu_min, dnu, nbins, cut, &lo[l], &hi[l]);
+}
+
+/* Pair count with one cutting length per line (cut_l[l] >= 0, in cm^-1). */
+int64_t hko_count_pairs_percut(int64_t n, const double *nu0, const double *cut_l, double nu_min,
+                               double dnu, int64_t nbins)
+{
+    int64_t total = 0;
+    const double q = 1.0 / dnu;
+#pragma omp parallel for schedule(static) reduction(+ : total)
+    for (int64_t l = 0; l < n; ++l) {
+        int64_t lo, hi;
+        line_range_w(nu0[l], nu_min, dnu, nbins, 0, cut_l[l] * q, &lo, &hi);
+        if (hi >= lo)
+            total += hi - lo + 1;
+    }
+    return total;
 }
 
 int64_t hko_count_pairs(int64_t n, const double *nu0, double nu_min, double dnu, int64_t nbins,
@@ -314,20 +353,35 @@ int64_t hko_count_pairs(int64_t n, const double *nu0, double nu_min, double dnu,
 /* sigma_out[j] = sigma(bin_lo + j) for j < bin_hi - bin_lo.  Lines need not be
  * sorted; if sorted_nu0 != 0 the candidate lines are narrowed by bisection on
  * nu0 (a superset; the cut predicate still decides).  Parallel over blocks of
- * bins; each bin sums its lines in ascending index order. */
-void hko_sigma(int64_t n, const double *nu0, const double *S, const double *alphaD,
-               const double *gammaL, int sorted_nu0, double nu_min, double dnu, int64_t nbins,
-               double cut, int64_t bin_lo, int64_t bin_hi, double *sigma_out, int nthreads)
+ * bins; each bin sums its lines in ascending index order.
+ * cut_l: NULL for the fixed cut `cut` (<= 0: no cut), else one cutting
+ * length per line (cm^-1, >= 0).  plinth: subtract from every bin inside a
+ * line's cut the line's own value at the cutting length,
+ * S Re w(cut_l / alpha_D + i y) / (alpha_D sqrt(pi)) (Sect. 2.1, "Removing
+ * the Plinth"); a line without a cut has no plinth. */
+void hko_sigma_ext(int64_t n, const double *nu0, const double *S, const double *alphaD,
+                   const double *gammaL, const double *cut_l, int plinth, int sorted_nu0,
+                   double nu_min, double dnu, int64_t nbins, double cut, int64_t bin_lo,
+                   int64_t bin_hi, double *sigma_out, int nthreads)
 {
     const double inv_sqrt_pi = 1.0 / sqrt(O_PI);
+    const double q = 1.0 / dnu;
     int64_t nb = bin_hi - bin_lo;
     if (nb <= 0)
         return;
     memset(sigma_out, 0, (size_t)nb * sizeof(double));
+    const int nocut = cut_l == NULL && !(cut > 0.0);
+    double cmax = cut;
+    if (cut_l) {
+        cmax = 0.0;
+        for (int64_t l = 0; l < n; ++l)
+            if (cut_l[l] > cmax)
+                cmax = cut_l[l];
+    }
     int64_t l_begin = 0, l_end = n;
-    if (sorted_nu0 && cut > 0.0 && n > 0) {
-        double lo_nu = nu_min + (double)bin_lo * dnu - cut - 2.0 * dnu;
-        double hi_nu = nu_min + (double)(bin_hi - 1) * dnu + cut + 2.0 * dnu;
+    if (sorted_nu0 && !nocut && n > 0) {
+        double lo_nu = nu_min + (double)bin_lo * dnu - cmax - 2.0 * dnu;
+        double hi_nu = nu_min + (double)(bin_hi - 1) * dnu + cmax + 2.0 * dnu;
         int64_t a = 0, b = n;
         while (a < b) {
             int64_t m = (a + b) / 2;
@@ -349,12 +403,13 @@ void hko_sigma(int64_t n, const double *nu0, const double *S, const double *alph
     int64_t blk = 64;
     int64_t nblk = (nb + blk - 1) / blk;
 #pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t q = 0; q < nblk; ++q) {
-        int64_t b0 = bin_lo + q * blk;
+    for (int64_t qb = 0; qb < nblk; ++qb) {
+        int64_t b0 = bin_lo + qb * blk;
         int64_t b1 = b0 + blk < bin_hi ? b0 + blk : bin_hi;
         for (int64_t l = l_begin; l < l_end; ++l) {
+            const double cl = cut_l ? cut_l[l] : cut;
             int64_t lo, hi;
-            line_range(nu0[l], nu_min, dnu, nbins, cut, &lo, &hi);
+            line_range_w(nu0[l], nu_min, dnu, nbins, nocut, cl * q, &lo, &hi);
             if (lo < b0) lo = b0;
             if (hi > b1 - 1) hi = b1 - 1;
             if (hi < lo)
@@ -362,12 +417,21 @@ void hko_sigma(int64_t n, const double *nu0, const double *S, const double *alph
             bin_pos p = line_pos(nu0[l], nu_min, dnu);
             double y = gammaL[l] / alphaD[l];
             double amp = S[l] * inv_sqrt_pi / alphaD[l];
+            double h = (plinth && !nocut) ? amp * creal(w_eval(cl / alphaD[l], y)) : 0.0;
             for (int64_t i = lo; i <= hi; ++i) {
                 double x = ((double)(i - p.i0) - p.r) * dnu / alphaD[l];
-                sigma_out[i - bin_lo] += amp * creal(w_eval(x, y));
+                sigma_out[i - bin_lo] += amp * creal(w_eval(x, y)) - h;
             }
         }
     }
+}
+
+void hko_sigma(int64_t n, const double *nu0, const double *S, const double *alphaD,
+               const double *gammaL, int sorted_nu0, double nu_min, double dnu, int64_t nbins,
+               double cut, int64_t bin_lo, int64_t bin_hi, double *sigma_out, int nthreads)
+{
+    hko_sigma_ext(n, nu0, S, alphaD, gammaL, NULL, 0, sorted_nu0, nu_min, dnu, nbins, cut,
+                  bin_lo, bin_hi, sigma_out, nthreads);
 }
 
 /* ---- adjoint (gradient of L = sum_i g_i sigma_i) ------------------------ */

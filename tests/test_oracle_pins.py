@@ -224,6 +224,82 @@ def test_cut_tie_is_inclusive_and_no_cut_is_full_grid():
     assert (lo[0], hi[0]) == (0, 99)
 
 
+# ------------------------------------------- plinth and per-line cuts (Sect. 2.1, 2.4.3) --
+
+def test_plinth_vanishes_at_the_cut_edge():
+    """A line on a bin centre with a cut of a whole number of bins: the bins at
+    +-cut sit exactly at the cutting length, so with the plinth removed they
+    are exactly zero; inside the cut the profile stays positive and equals the
+    un-removed one minus a constant."""
+    nu_min, dnu, nbins = 0.0, 0.125, 200                # binary-exact grid
+    nu0, S, aD, GL, cut = 10.0, 3e-21, 0.21, 0.07, 2.5    # u = 80, W = 20 exactly
+    a = oracle.sigma(np.array([nu0]), np.array([S]), np.array([aD]), np.array([GL]), nu_min,
+                     dnu, nbins, cut)
+    b = oracle.sigma(np.array([nu0]), np.array([S]), np.array([aD]), np.array([GL]), nu_min,
+                     dnu, nbins, cut, plinth=True)
+    assert b[60] == 0.0 and b[100] == 0.0
+    assert np.all(b[61:100] > 0) and np.all(b[:60] == 0) and np.all(b[101:] == 0)
+    d = a[60:101] - b[60:101]          # rounding of a - h is ~1e-16 of a, a up to 1e3 h
+    assert np.all(np.abs(d - d[0]) <= 4e-16 * a[60:101]) and d[0] > 0
+
+
+def test_plinth_area_lorentz_and_gauss_limits():
+    """Area of the plinth-removed profile against closed forms: Lorentzian
+    (alpha_D << Gamma_L) (2/pi) atan(c/G) - 2 c G / (pi (c^2 + G^2)); Gaussian
+    (Gamma_L = 0) erf(c/alpha_D) - 2 c exp(-c^2/alpha_D^2) / (alpha_D sqrt(pi))."""
+    dnu = 0.0005
+    grid = (0.0, dnu, 40000)
+    nu0 = 10.00025                                      # halfway between bins
+    S = 1.0
+    G, aD, c = 0.1, 1e-5, 2.0                            # Lorentzian limit, (aD/G)^2 = 1e-8
+    sig = oracle.sigma(np.array([nu0]), np.array([S]), np.array([aD]), np.array([G]), *grid, c,
+                       plinth=True)
+    # the cut edges fall on half-bins: midpoint rule, whose leading error for the
+    # kinked profile is (dnu^2 / 12) |phi'(c)| (Euler-Maclaurin)
+    exact = 2 / math.pi * math.atan(c / G) - 2 * c * G / (math.pi * (c * c + G * G))
+    exact += dnu ** 2 / 12 * (G / math.pi) * 2 * c / (c * c + G * G) ** 2
+    assert abs(sig.sum() * dnu - exact) < 2e-8 * exact
+    aD, c = 0.05, 0.1
+    sig = oracle.sigma(np.array([nu0]), np.array([S]), np.array([aD]), np.array([0.0]), *grid, c,
+                       plinth=True)
+    phic = math.exp(-(c / aD) ** 2) / (aD * SQPI)
+    exact = math.erf(c / aD) - 2 * c * phic
+    exact += dnu ** 2 / 12 * 2 * c / aD ** 2 * phic
+    assert abs(sig.sum() * dnu - exact) < 1e-9 * exact
+
+
+def test_per_line_cuts_doppler_and_lorentz():
+    """Doppler-multiple cuts: factor * sqrt(ln 2) * alpha_D with alpha_D from
+    Eq. gammaD in mpmath; Lorentz-multiple cuts: factor * Gamma_L.  The pair
+    count equals the exact rational count of bins with |nu_i - nu0| <= cut_l."""
+    rng = np.random.default_rng(31)
+    n = 200
+    nu0 = np.sort(rng.uniform(1.0, 300.0, n))
+    T, m = 1700.0, 18.0
+    g = json.load(open(GOLDEN))
+    c, kB, amu = g["c"]["value"], g["k_B"]["value"], 1.660538921e-24   # amu: CODATA 2010
+    aD, GL = oracle.widths(nu0, rng.uniform(0.01, 0.1, n), rng.uniform(0.3, 0.8, n), T, 0.7, m)
+    f = 37.0
+    cd = oracle.line_cuts(nu0, GL, oracle.CUT_DOPPLER, f, T, m)
+    with mp.workdps(40):
+        for l in range(0, n, 17):
+            ref = f * mp.sqrt(mp.log(2)) * mp.mpf(nu0[l]) / mp.mpf(c) * mp.sqrt(
+                2 * mp.mpf(kB) * T / (m * mp.mpf(amu)))
+            assert abs(cd[l] - float(ref)) <= 4e-16 * float(ref)
+    cl = oracle.line_cuts(nu0, GL, oracle.CUT_LORENTZ, 3.0, T, m)
+    assert np.allclose(cl, 3.0 * GL, rtol=1e-15, atol=0)
+    nu_min, dnu, nbins = 0.0, 0.01, 30000
+    for cuts in (cd, cl):
+        exact = 0
+        for l in range(n):
+            v, cf = Fraction(float(nu0[l])), Fraction(float(cuts[l]))
+            i0 = int(nu0[l] / dnu)
+            k = int(cuts[l] / dnu) + 3
+            exact += sum(1 for i in range(max(0, i0 - k), min(nbins, i0 + k + 1))
+                         if abs(Fraction(nu_min) + i * Fraction(dnu) - v) <= cf)
+        assert oracle.count_pairs_percut(nu0, cuts, nu_min, dnu, nbins) == exact
+
+
 # ------------------------------------------------------------ sigma: limits --
 
 def _single(nu0, S, aD, GL, grid, cut):
