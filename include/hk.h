@@ -79,14 +79,25 @@ extern "C" {
                       sigma out as float */
 #define HK_FP64 1  /* FP64 throughout; sigma out as double */
 /* cut mode (Sect. 2.4.3 item 4) */
-#define HK_CUT_FIXED 0 /* |nu_i - nu0| <= cut; cut <= 0 means the whole grid */
-#define HK_CUT_NONE 1  /* every bin of the grid */
+#define HK_CUT_FIXED 0   /* |nu_i - nu0| <= cut; cut <= 0 means the whole grid */
+#define HK_CUT_NONE 1    /* every bin of the grid */
+#define HK_CUT_DOPPLER 2 /* per line: |nu_i - nu0| <= cut * Gamma_D, Gamma_D = sqrt(ln 2)
+                            alpha_D the Doppler half width (Eq. gammaD), evaluated in
+                            FP64 as cut * (nu0 * K_D), K_D = sqrt(ln 2) sqrt(2 k_B T/m)/c */
+#define HK_CUT_LORENTZ 3 /* per line: |nu_i - nu0| <= cut * Gamma_L, the Lorentz half
+                            width in FP64 (a bin within one ulp of such a boundary may be
+                            decided differently from a CPU evaluation: pow differs in its
+                            last bit between math libraries) */
 /* flags */
 #define HK_PER_GRAM 1u  /* divide S by the molecular mass in grams (Eq. S units) */
 #define HK_SIGMA_F64 2u /* HK_FP32C: write sigma as double instead of float.  The
                            FP32C arithmetic is unchanged; use it when S(T) can exceed
                            the float range (S_ref scaled to T >> T_ref for lines of
                            large E'' gives S(T) ~ 1e40 and more) */
+#define HK_REMOVE_PLINTH 4u /* subtract from every bin inside a line's cut the line's own
+                               value at its cutting length, S phi(nu0 + cut) (Sect. 2.1,
+                               "Removing the Plinth"); no effect without a cut.  Not
+                               supported by hk_cross_section_backward (HK_ENOTSUP) */
 
 /* ---- data structures ---------------------------------------------------- */
 
@@ -127,8 +138,13 @@ typedef struct {
 
 /* Options.  T_ref, P_ref, Q_Tref: reference state of S_ref and gamma_ref
  * (296 K, 1 bar in the benchmark configurations).  cut: cutting length in
- * cm^-1 (HK_CUT_FIXED); cut <= 0 means no cut.  precision: HK_FP32C or
- * HK_FP64.  flags: HK_PER_GRAM, HK_SIGMA_F64. */
+ * cm^-1 (HK_CUT_FIXED; cut <= 0 means no cut), or the factor (> 0) of the
+ * per-line half width (HK_CUT_DOPPLER, HK_CUT_LORENTZ; Sect. 2.4.3 item 4:
+ * fixed length, Doppler or Lorentz half-width multiples).  precision:
+ * HK_FP32C or HK_FP64.  flags: HK_PER_GRAM, HK_SIGMA_F64, HK_REMOVE_PLINTH.
+ * The per-line cut modes and the plinth apply to every sigma entry point;
+ * hk_voigt_accumulate takes its own fixed cut, and hk_cross_section_backward
+ * supports HK_CUT_FIXED / HK_CUT_NONE without the plinth (else HK_ENOTSUP). */
 typedef struct {
     double T_ref;
     double P_ref;

@@ -174,11 +174,18 @@ static int check_opts(const hk_opts *o)
     if (!o || !finite_pos(o->T_ref) || !finite_pos(o->P_ref) || !finite_pos(o->Q_Tref) ||
         !std::isfinite(o->cut))
         return HK_EINVAL;
-    if (o->cut_mode != HK_CUT_FIXED && o->cut_mode != HK_CUT_NONE) return HK_EINVAL;
+    if (o->cut_mode != HK_CUT_FIXED && o->cut_mode != HK_CUT_NONE &&
+        o->cut_mode != HK_CUT_DOPPLER && o->cut_mode != HK_CUT_LORENTZ)
+        return HK_EINVAL;
+    if ((o->cut_mode == HK_CUT_DOPPLER || o->cut_mode == HK_CUT_LORENTZ) && !(o->cut > 0.0))
+        return HK_EINVAL;
     if (o->precision != HK_FP32C && o->precision != HK_FP64) return HK_EINVAL;
-    if (o->flags & ~(HK_PER_GRAM | HK_SIGMA_F64)) return HK_EINVAL;
+    if (o->flags & ~(HK_PER_GRAM | HK_SIGMA_F64 | HK_REMOVE_PLINTH)) return HK_EINVAL;
     return HK_OK;
 }
+static_assert(kCutFixed == HK_CUT_FIXED && kCutNone == HK_CUT_NONE &&
+                  kCutDoppler == HK_CUT_DOPPLER && kCutLorentz == HK_CUT_LORENTZ,
+              "cut mode values");
 
 // The FP32 fast path of the cut bounds: W = Wi + Wf for 0 < W < 2^30.
 static void set_cut_split(GridD *d)
@@ -199,11 +206,16 @@ static GridD make_grid(const hk_grid *g, const hk_opts *o)
     d.dnu = g->dnu;
     d.inv_dnu = 1.0 / g->dnu;
     d.nbins = g->nbins;
-    bool nocut = (o && o->cut_mode == HK_CUT_NONE) || !o;
+    const int mode = o ? o->cut_mode : HK_CUT_NONE;
+    const bool perline = mode == HK_CUT_DOPPLER || mode == HK_CUT_LORENTZ;
+    bool nocut = mode == HK_CUT_NONE || perline;   // no fixed cut
     d.cut = nocut ? 0.0 : o->cut;
     d.W = (d.cut > 0.0) ? d.cut * d.inv_dnu : 0.0;
     if (d.cut <= 0.0) d.cut = 0.0;
     set_cut_split(&d);
+    d.cut_mode = d.W > 0.0 ? HK_CUT_FIXED : (perline ? mode : HK_CUT_NONE);
+    d.cut_factor = perline ? o->cut : 0.0;
+    d.plinth = (o && (o->flags & HK_REMOVE_PLINTH)) ? 1 : 0;
     return d;
 }
 
@@ -217,6 +229,9 @@ static GridD make_grid_cut(const hk_grid *g, double cut)
     d.cut = cut > 0.0 ? cut : 0.0;
     d.W = cut > 0.0 ? cut * d.inv_dnu : 0.0;
     set_cut_split(&d);
+    d.cut_mode = d.W > 0.0 ? HK_CUT_FIXED : HK_CUT_NONE;
+    d.cut_factor = 0.0;
+    d.plinth = 0;
     return d;
 }
 
@@ -267,6 +282,9 @@ static Prob make_prob(const hk_lines *L, const hk_state *s, const hk_opts *o)
     p.press = s->P / o->P_ref;
     p.inv_Pref = 1.0 / o->P_ref;
     p.nat_coef = 1.0 / (4.0 * kPI * kC);
+    p.tratio = o->T_ref / T;
+    // the same operations, in the same order, as the oracle's Doppler cut width
+    p.K_D = std::sqrt(0.6931471805599453) * std::sqrt(2.0 * kKB * T / m_g) / kC;
     set_f32_scalars(&p);
     return p;
 }
@@ -874,6 +892,9 @@ int hk_cross_section_backward(const hk_lines *lines, const hk_grid *grid, const 
     if (!TP || nTP <= 0 || !grad_sigma || !dL_dT || !dL_dP) return HK_EINVAL;
     if (lines->n > 0 && (!dL_dSref || !dL_dgamma_ref)) return HK_EINVAL;
     if (lines->s_mode != HK_S_REF) return HK_ENOTSUP;
+    if (opts->cut_mode == HK_CUT_DOPPLER || opts->cut_mode == HK_CUT_LORENTZ ||
+        (opts->flags & HK_REMOVE_PLINTH))
+        return HK_ENOTSUP;
     for (int k = 0; k < nTP; ++k)
         if ((rc = check_state(&TP[k]))) return rc;
     size_t need;

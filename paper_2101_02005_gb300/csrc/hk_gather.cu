@@ -40,7 +40,7 @@ constexpr int CHUNK = NTHREADS;  // lines staged per pass: one prologue thread p
 constexpr int FLUSH = 32;        // FP32 lines per two-sum fold
 
 template <typename R> struct LineT {
-    R b, r, y, s;
+    R b, r, y, s, h;   // h: the plinth s Re w(x_cut + iy), or 0
     int i0, lo, hi, pad;
 };
 
@@ -94,6 +94,27 @@ __global__ void k_scale_prepass(const Prob *__restrict__ probs, int nprob, GridD
     if ((threadIdx.x & 31) == 0 && emax != INT_MIN) atomicMax(pr.scale_exp, emax);
 }
 
+// ---- largest per-line cutting length (per-line cut modes) --------------------
+// Non-negative doubles order like their bit patterns, so an integer atomicMax
+// on the bits is a max on the values.
+__global__ void k_cut_max(const Prob *__restrict__ probs, int nprob, GridD g)
+{
+    int p = blockIdx.y;
+    if (p >= nprob) return;
+    const Prob &pr = probs[p];
+    unsigned long long best = 0ull;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pr.n;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        const double nu0 = pr.nu0[l];
+        if (!(nu0 > 0.0)) continue;
+        const CutW cw = line_cut(pr, g, l, nu0);
+        const double cut = __dmul_rn(cw.W, g.dnu) * (1.0 + 1e-12) + 1e-300;  // >= the cut
+        if (cut > 0.0 && cut < 1e300) best = max(best, (unsigned long long)__double_as_longlong(cut));
+    }
+    for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best) atomicMax((unsigned long long *)pr.cutmax, best);
+}
+
 // ---- tile line ranges and item counts ---------------------------------------
 __device__ __forceinline__ int64_t lower_bound_nu(const double *nu, int64_t n, double v)
 {
@@ -124,9 +145,10 @@ __global__ void k_tile_ranges(const Prob *__restrict__ probs, int nprob, GridD g
     int64_t t = idx - (int64_t)p * ntiles;
     const Prob &pr = probs[p];
     int64_t lb = 0, le = pr.n;
-    if (g.W > 0.0) {
-        double lo_nu = g.nu_min + (double)(t * tile_bins) * g.dnu - g.cut - 2.0 * g.dnu;
-        double hi_nu = g.nu_min + (double)(t * tile_bins + tile_bins - 1) * g.dnu + g.cut + 2.0 * g.dnu;
+    if (has_cut(g)) {
+        const double cut = g.W > 0.0 ? g.cut : *pr.cutmax;
+        double lo_nu = g.nu_min + (double)(t * tile_bins) * g.dnu - cut - 2.0 * g.dnu;
+        double hi_nu = g.nu_min + (double)(t * tile_bins + tile_bins - 1) * g.dnu + cut + 2.0 * g.dnu;
         lb = lower_bound_nu(pr.nu0, pr.n, lo_nu);
         le = upper_bound_nu(pr.nu0, pr.n, hi_nu);
     }
@@ -168,7 +190,8 @@ __device__ __forceinline__ void stage_line(const Prob &pr, const GridD &g, int64
     double nu0 = pr.nu0[l];
     int i0, lo, hi;
     double r;
-    bool any = line_geometry(nu0, g, &i0, &r, &lo, &hi);
+    const CutW cw = line_cut(pr, g, l, nu0);
+    bool any = line_geometry_w(nu0, g, cw.nocut, cw.W, &i0, &r, &lo, &hi);
     LineT<R> q;
     int c;
     double rn;
@@ -211,6 +234,8 @@ __device__ __forceinline__ void stage_line(const Prob &pr, const GridD &g, int64
         q.b = (R)(g.dnu * aDinv);
         q.y = (R)y;
     }
+    // the plinth: this line's value at its cutting length, x_cut = W b
+    q.h = (g.plinth && any && !cw.nocut) ? q.s * voigt_re<R>((R)cw.W * q.b, q.y) : R(0);
     *out = q;
     *nu_out = nu0;
 }
@@ -276,8 +301,9 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         const int scale = (sizeof(R) == 4) ? *pr.scale_exp : 0;
 
         const int wb0 = (int)(t * TILE) + warp * 32 * BPT;  // first bin of this warp
-        const double wnu_lo = g.nu_min + (double)wb0 * g.dnu - g.cut - 2.0 * g.dnu;
-        const double wnu_hi = g.nu_min + (double)(wb0 + 32 * BPT - 1) * g.dnu + g.cut + 2.0 * g.dnu;
+        const double wcut = g.W > 0.0 ? g.cut : (has_cut(g) ? *pr.cutmax : 0.0);
+        const double wnu_lo = g.nu_min + (double)wb0 * g.dnu - wcut - 2.0 * g.dnu;
+        const double wnu_hi = g.nu_min + (double)(wb0 + 32 * BPT - 1) * g.dnu + wcut + 2.0 * g.dnu;
 
         R acc[BPT], shi[BPT], slo[BPT];
 #pragma unroll
@@ -291,7 +317,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
             __syncthreads();
             // this warp's candidate lines inside the chunk (bisection on nu0)
             int a = 0, b = nl;
-            if (g.W > 0.0) {
+            if (has_cut(g)) {
                 int lo = 0, hi = nl;
                 while (lo < hi) {
                     int m = (lo + hi) >> 1;
@@ -321,7 +347,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
                 for (int j = 0; j < BPT; ++j) {
                     const bool inr = (unsigned)(kk + 32 * j) <= span;
                     const R x = fma(kf0 + R(32 * j), q.b, -rb);
-                    const R v = pair_value<R>(x, y, Y, q.s, sy);
+                    const R v = pair_value<R>(x, y, Y, q.s, sy) - q.h;
                     acc[j] += inr ? v : R(0);
                 }
                 if (sizeof(R) == 4 && ++nsince == FLUSH) {
@@ -390,7 +416,8 @@ __global__ void k_count_pairs(Prob p, GridD g, unsigned long long *counts)
         // the FP32 kernels' geometry (its pair total must equal the oracle's)
         int cb, lo, hi;
         float rnf;
-        if (!line_geometry_f32(p.nu0[l], g, &cb, &rnf, &lo, &hi)) continue;
+        const double nu0 = p.nu0[l];
+        if (!line_geometry_f32(nu0, g, line_cut(p, g, l, nu0), &cb, &rnf, &lo, &hi)) continue;
         const double r = (double)rnf;
         double S, aDinv, y;
         line_strength_f64(p, l, &S, &aDinv, &y);
@@ -545,6 +572,7 @@ size_t gather_workspace(int nprob, int64_t nbins, int precision, int bpt)
     add(sizeof(int64_t) * m);       // counts
     add(sizeof(int64_t) * (m + 1)); // item_off
     add(sizeof(unsigned long long) * 2);
+    add(sizeof(double) * nprob);    // largest per-line cut
     if (precision == 0) add(sizeof(double) * (size_t)nprob * nbins);
     return bytes;
 }
@@ -569,6 +597,7 @@ int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt,
     int64_t *counts = (int64_t *)take(sizeof(int64_t) * m);
     int64_t *item_off = (int64_t *)take(sizeof(int64_t) * (m + 1));
     unsigned long long *counter = (unsigned long long *)take(sizeof(unsigned long long) * 2);
+    double *cutmax = (double *)take(sizeof(double) * nprob);
     // counter[0]: next work item of the persistent gather
     double *acc = nullptr;
     if (precision == 0) acc = (double *)take(sizeof(double) * (size_t)nprob * g.nbins);
@@ -577,6 +606,7 @@ int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt,
     for (int p = 0; p < nprob; ++p) {
         probs_h[p].status = status_d;
         probs_h[p].scale_exp = scales + p;
+        probs_h[p].cutmax = cutmax + p;
         if (precision == 0) probs_h[p].acc = acc + (size_t)p * g.nbins;
         else probs_h[p].acc = (double *)out + (size_t)p * g.nbins;
     }
@@ -596,6 +626,12 @@ int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt,
     } else if (!accumulate) {
         if ((e = cudaMemsetAsync(out, 0, sizeof(double) * (size_t)nprob * g.nbins, st)))
             return fail_cuda(e);
+    }
+    if (g.cut_mode == kCutDoppler || g.cut_mode == kCutLorentz) {
+        if ((e = cudaMemsetAsync(cutmax, 0, sizeof(double) * nprob, st))) return fail_cuda(e);
+        dim3 grid(num_sms * 4, nprob);
+        k_cut_max<<<grid, 256, 0, st>>>(probs_d, nprob, g);
+        if ((e = cudaGetLastError())) return fail_cuda(e);
     }
     {
         int64_t blocks = (m + 255) / 256;

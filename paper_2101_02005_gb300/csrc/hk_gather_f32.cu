@@ -47,7 +47,7 @@ struct __align__(16) Rec {
     float b, rn, Y, s;          // x step per bin, centre offset from bin c, y^2, scaled strength
     float rnb, sy, sy2, Yq;     // rn b, s y / sqrt(pi), sy / 2, Y + 1/4             (2 nodes)
     float Ca, Cb, sa, sb;       // 2 tau Y + tau^2 for both 4-node pairs, 2 W sy      (4 nodes)
-    float y;                    // Gamma_L / alpha_D
+    float y, h;                 // Gamma_L / alpha_D; the plinth s Re w(x_cut + iy) (or 0)
     int c, lo, hi;              // nearest bin to the centre, inclusive bin range in the cut
     int gA, gB, L2, R2;         // the line's groups; groups of band gh2 or inner
     int L4, R4, Lc, Rc;         // groups of band gh4 or inner; groups holding core bins
@@ -96,7 +96,9 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
     Rec q;
     int c, lo, hi;
     float rn;
-    const bool any = line_geometry_f32(pr.nu0[l], g, &c, &rn, &lo, &hi);
+    const double nu0 = pr.nu0[l];
+    const CutW cw = line_cut(pr, g, l, nu0);
+    const bool any = line_geometry_f32(nu0, g, cw, &c, &rn, &lo, &hi);
     q.c = c;
     q.lo = lo;
     q.hi = hi;
@@ -129,6 +131,8 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
     q.Cb = fmaf(2.0f * kTb, Y, kTb * kTb);
     q.sa = sy * kWa;
     q.sb = sy * kWb;
+    // the plinth: this line's value at its cutting length, x_cut = W b
+    q.h = (g.plinth && any && !cw.nocut) ? sv * voigt_re<float>((float)cw.W * b, y) : 0.0f;
     if (any) {
         q.gA = lo >> 5;
         q.gB = hi >> 5;
@@ -143,7 +147,7 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
 }
 
 // Value of one pair in band BAND at offset kf (float bin offset from c).
-template <int BAND> __device__ __forceinline__ float pair_f(const Rec &q, float kf)
+template <int BAND> __device__ __forceinline__ float pair_raw(const Rec &q, float kf)
 {
     const float x = fmaf(kf, q.b, -q.rnb);
     const float X = x * x;
@@ -162,24 +166,34 @@ template <int BAND> __device__ __forceinline__ float pair_f(const Rec &q, float 
     }
 }
 
+// Launch variants V: bit 1 peels the edge groups (wide lines), bit 2 removes
+// the plinth (every in-range pair less the line's value at its cut).
+constexpr int kVPeel = 1, kVPlinth = 2;
+
+template <int BAND, int V> __device__ __forceinline__ float pair_f(const Rec &q, float kf)
+{
+    const float v = pair_raw<BAND>(q, kf);
+    return (V & kVPlinth) ? v - q.h : v;
+}
+
 // One masked group: lanes add only where bin 32 g + lane lies in the line's
 // range [lo, hi].
-template <int BAND>
+template <int BAND, int V>
 __device__ __forceinline__ void edge_group(const Rec &q, int g, int tg0, float *base, int kfc,
                                            int lane)
 {
     if ((unsigned)(32 * g + lane - q.lo) <= (unsigned)(q.hi - q.lo))
-        base[32 * (g - tg0)] += pair_f<BAND>(q, (float)(32 * g + kfc));
+        base[32 * (g - tg0)] += pair_f<BAND, V>(q, (float)(32 * g + kfc));
 }
 
 // One band over groups [g0, g1] (inclusive), clipped to [lo_g, hi_g].  `base`
 // is the warp's tile copy at group tg0 plus this lane; kfc = lane - c.  Only
-// the line's first and last groups (gA, gB) can be partial.  PEEL = false: a
-// lane adds only if its bin lies in the line's range (one compare per group,
-// best for lines a few groups wide); PEEL = true: gA and gB are peeled off
-// and masked, the groups between them run unmasked (best for wide lines,
+// the line's first and last groups (gA, gB) can be partial.  Without kVPeel
+// a lane adds only if its bin lies in the line's range (one compare per
+// group, best for lines a few groups wide); with kVPeel gA and gB are peeled
+// off and masked, the groups between them run unmasked (best for wide lines,
 // where the per-band test costs less than the per-group one).
-template <int BAND, bool PEEL>
+template <int BAND, int V>
 __device__ __forceinline__ void sweep(const Rec &q, int g0, int g1, int lo_g, int hi_g, int tg0,
                                       float *base, int kfc, int lane)
 {
@@ -188,25 +202,25 @@ __device__ __forceinline__ void sweep(const Rec &q, int g0, int g1, int lo_g, in
     if (g0 > g1) return;
     float kf;
     float *p, *pe;
-    if (PEEL) {
+    if (V & kVPeel) {
         if (g0 == q.gA) {
-            edge_group<BAND>(q, g0, tg0, base, kfc, lane);
+            edge_group<BAND, V>(q, g0, tg0, base, kfc, lane);
             if (++g0 > g1) return;
         }
         if (g1 == q.gB) {
-            edge_group<BAND>(q, g1, tg0, base, kfc, lane);
+            edge_group<BAND, V>(q, g1, tg0, base, kfc, lane);
             if (--g1 < g0) return;
         }
         kf = (float)(32 * g0 + kfc);
         p = base + 32 * (g0 - tg0);
         pe = base + 32 * (g1 - tg0);
         for (; p < pe; p += 64, kf += 64.0f) {   // two groups per step
-            const float v0 = pair_f<BAND>(q, kf);
-            const float v1 = pair_f<BAND>(q, kf + 32.0f);
+            const float v0 = pair_f<BAND, V>(q, kf);
+            const float v1 = pair_f<BAND, V>(q, kf + 32.0f);
             p[0] += v0;
             p[32] += v1;
         }
-        if (p == pe) p[0] += pair_f<BAND>(q, kf);
+        if (p == pe) p[0] += pair_f<BAND, V>(q, kf);
     } else {
         const unsigned span = (unsigned)(q.hi - q.lo);
         unsigned rel = (unsigned)(32 * g0 + lane - q.lo);   // bin - lo
@@ -214,12 +228,12 @@ __device__ __forceinline__ void sweep(const Rec &q, int g0, int g1, int lo_g, in
         p = base + 32 * (g0 - tg0);
         pe = base + 32 * (g1 - tg0);
         for (; p < pe; p += 64, kf += 64.0f, rel += 64u) {   // two groups per step
-            const float v0 = pair_f<BAND>(q, kf);
-            const float v1 = pair_f<BAND>(q, kf + 32.0f);
+            const float v0 = pair_f<BAND, V>(q, kf);
+            const float v1 = pair_f<BAND, V>(q, kf + 32.0f);
             if (rel <= span) p[0] += v0;
             if (rel + 32u <= span) p[32] += v1;
         }
-        if (p == pe && rel <= span) p[0] += pair_f<BAND>(q, kf);
+        if (p == pe && rel <= span) p[0] += pair_f<BAND, V>(q, kf);
     }
 }
 
@@ -229,13 +243,14 @@ __device__ __forceinline__ void core_entry(Smem &S, int warp, int t0, unsigned e
     const int tidx = (int)(e & 0xffffu);
     const float kk = (float)(t0 + tidx - qq.c);
     const float xx = fmaf(kk, qq.b, -qq.rnb);
-    atomicAdd(&S.acc[warp][tidx], qq.s * core_re<float>(xx, qq.y));
+    atomicAdd(&S.acc[warp][tidx], qq.s * core_re<float>(xx, qq.y) - qq.h);
 }
 
 // Groups holding core bins: lanes with r2 >= 64 take the 4-node rule (valid
 // for every r2 >= 64) in place; core lanes (r2 < 64) are queued as (record
 // slot, tile index) and the queue is evaluated 32 entries at a time with the
 // trapezoid rule.
+template <int V>
 __device__ __forceinline__ void sweep_core(const Rec &q, int slot, int g0, int g1, int lo_g,
                                            int hi_g, int tg0, float *base, int kfc, int lane,
                                            unsigned *queue, int &qn, Smem &S, int warp, int t0)
@@ -249,7 +264,7 @@ __device__ __forceinline__ void sweep_core(const Rec &q, int slot, int g0, int g
         const float x = fmaf(kf, q.b, -q.rnb);
         const float r2 = fmaf(x, x, q.Y);
         const bool core = act && r2 < 64.0f;
-        if (act && !core) base[32 * (g - tg0)] += pair_f<kBandGH4>(q, kf);
+        if (act && !core) base[32 * (g - tg0)] += pair_f<kBandGH4, V>(q, kf);
         const unsigned m = __ballot_sync(0xffffffffu, core);
         if (m) {
             const int pos = qn + __popc(m & ((1u << lane) - 1u));
@@ -278,7 +293,7 @@ __device__ __forceinline__ void drain_rest(unsigned *queue, int &qn, Smem &S, in
 }
 
 // All of one line's bins inside the tile (groups [tg0, tg1]).
-template <bool PEEL>
+template <int V>
 __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1, float *base,
                                         int lane, unsigned *queue, int &qn, Smem &S, int warp,
                                         int t0)
@@ -286,14 +301,14 @@ __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1
     const int ga = max(q.gA, tg0), gb = min(q.gB, tg1);
     if (ga > gb) return;  // warp-uniform
     const int kfc = lane - q.c;
-    sweep<kBandGH1, PEEL>(q, q.gA, q.L2 - 1, ga, gb, tg0, base, kfc, lane);
-    sweep<kBandGH2, PEEL>(q, q.L2, q.L4 - 1, ga, gb, tg0, base, kfc, lane);
-    sweep<kBandGH4, PEEL>(q, q.L4, q.Lc - 1, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH1, V>(q, q.gA, q.L2 - 1, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH2, V>(q, q.L2, q.L4 - 1, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH4, V>(q, q.L4, q.Lc - 1, ga, gb, tg0, base, kfc, lane);
     if (q.Lc <= q.Rc)
-        sweep_core(q, slot, q.Lc, q.Rc, ga, gb, tg0, base, kfc, lane, queue, qn, S, warp, t0);
-    sweep<kBandGH4, PEEL>(q, q.Rc + 1, q.R4, ga, gb, tg0, base, kfc, lane);
-    sweep<kBandGH2, PEEL>(q, q.R4 + 1, q.R2, ga, gb, tg0, base, kfc, lane);
-    sweep<kBandGH1, PEEL>(q, q.R2 + 1, q.gB, ga, gb, tg0, base, kfc, lane);
+        sweep_core<V>(q, slot, q.Lc, q.Rc, ga, gb, tg0, base, kfc, lane, queue, qn, S, warp, t0);
+    sweep<kBandGH4, V>(q, q.Rc + 1, q.R4, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH2, V>(q, q.R4 + 1, q.R2, ga, gb, tg0, base, kfc, lane);
+    sweep<kBandGH1, V>(q, q.R2 + 1, q.gB, ga, gb, tg0, base, kfc, lane);
 }
 
 __device__ __forceinline__ void fold(Smem &S, int tid)
@@ -312,7 +327,7 @@ __device__ __forceinline__ void fold(Smem &S, int tid)
     }
 }
 
-template <bool PEEL>
+template <int V>
 __global__ void __launch_bounds__(NT, 3)
     k_gather_f32(const Prob *__restrict__ probs, GridD g, int64_t ntiles, int64_t m,
                  const int64_t *__restrict__ item_off, const int64_t *__restrict__ tile_lb,
@@ -379,7 +394,7 @@ __global__ void __launch_bounds__(NT, 3)
                 // a register copy: the record must not be re-read from shared
                 // memory after every store into the tile copy
                 const Rec q = S.rec[warp][j];
-                do_line<PEEL>(q, j, tg0, tg1, accb, lane, queue, qn, S, warp, t0);
+                do_line<V>(q, j, tg0, tg1, accb, lane, queue, qn, S, warp, t0);
             }
             drain_rest(queue, qn, S, warp, lane, t0);
             if (++rounds == FLUSH_ROUNDS) {
@@ -409,7 +424,7 @@ size_t gather_f32_smem() { return sizeof(f32g::Smem); }
 // Lines at least this many bins wide take the peeled sweeps.
 constexpr double kPeelBins = 1024.0;
 
-template <bool PEEL>
+template <int V>
 static int launch_variant(const Prob *probs_d, const GridD &g, int64_t ntiles, int64_t m,
                           const int64_t *item_off, const int64_t *tile_lb,
                           const int64_t *tile_le, int lmax, unsigned long long *counter,
@@ -419,16 +434,16 @@ static int launch_variant(const Prob *probs_d, const GridD &g, int64_t ntiles, i
     static int per_sm = 0;
     cudaError_t e;
     if (!configured) {
-        e = cudaFuncSetAttribute(f32g::k_gather_f32<PEEL>,
+        e = cudaFuncSetAttribute(f32g::k_gather_f32<V>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(f32g::Smem));
         if (e) return fail_cuda(e);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32g::k_gather_f32<PEEL>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32g::k_gather_f32<V>,
                                                           f32g::NT, sizeof(f32g::Smem));
         if (e || per_sm < 1) per_sm = 1;
         configured = true;
     }
-    f32g::k_gather_f32<PEEL><<<num_sms * per_sm, f32g::NT, sizeof(f32g::Smem), st>>>(
+    f32g::k_gather_f32<V><<<num_sms * per_sm, f32g::NT, sizeof(f32g::Smem), st>>>(
         probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter);
     e = cudaGetLastError();
     return e ? fail_cuda(e) : HK_OK;
@@ -439,10 +454,21 @@ int gather_f32_launch(const Prob *probs_d, const GridD &g, int64_t ntiles, int64
                       int lmax, unsigned long long *counter, cudaStream_t st, int num_sms)
 {
     const bool wide = g.W <= 0.0 || 2.0 * g.W + 1.0 >= kPeelBins;
-    return wide ? launch_variant<true>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
-                                       counter, st, num_sms)
-                : launch_variant<false>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
-                                        counter, st, num_sms);
+    const int v = (wide ? f32g::kVPeel : 0) | (g.plinth && has_cut(g) ? f32g::kVPlinth : 0);
+    switch (v) {
+    case 0:
+        return launch_variant<0>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
+                                 counter, st, num_sms);
+    case 1:
+        return launch_variant<1>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
+                                 counter, st, num_sms);
+    case 2:
+        return launch_variant<2>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
+                                 counter, st, num_sms);
+    default:
+        return launch_variant<3>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
+                                 counter, st, num_sms);
+    }
 }
 
 }  // namespace hk

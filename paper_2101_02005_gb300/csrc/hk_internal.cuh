@@ -247,6 +247,9 @@ struct Prob {
     double press;               // P / P_ref
     double inv_Pref;            // 1 / P_ref
     double nat_coef;            // 1 / (4 pi c)
+    double tratio;              // T_ref / T
+    double K_D;                 // sqrt(ln 2) sqrt(2 k_B T / m) / c: Gamma_D = nu0 K_D
+    const double *cutmax;       // device: largest cutting length of the lines (per-line modes)
     // the same scalars rounded to float (set with them on the host), for the
     // FP32 strength; K2 as a float pair K2_hi + K2_lo (about 48 bits)
     float qratio_f, c2T_f, c2Tref_f, mass_scale_f, aD_coef_f, log2_tratio_f, press_f,
@@ -261,14 +264,26 @@ struct Prob {
 constexpr unsigned kStatusRange = 1u;    // a float output overflowed
 constexpr unsigned kStatusTimeout = 2u;  // a bounded device wait gave up
 
+// Cut modes (the values of HK_CUT_* in hk.h).
+constexpr int kCutFixed = 0, kCutNone = 1, kCutDoppler = 2, kCutLorentz = 3;
+
 struct GridD {
     double nu_min, dnu, inv_dnu;
-    double W;                   // cut / dnu (as cut * inv_dnu); <= 0: no cut
-    double cut;
+    double W;                   // fixed cut / dnu (as cut * inv_dnu); <= 0: no fixed cut
+    double cut;                 // fixed cut, cm^-1 (0 without one)
     int64_t nbins;
     int Wi;                     // floor(W) for 0 < W < 2^30, else -1 (no fast cut path)
     float Wf;                   // W - Wi rounded to float
+    int cut_mode;               // kCut*: per-line modes take cut_factor times a half width
+    double cut_factor;
+    int plinth;                 // subtract each line's value at its cutting length
 };
+
+// Whether the lines have a cut at all (fixed or per line).
+__device__ __host__ __forceinline__ bool has_cut(const GridD &g)
+{
+    return g.cut_mode == kCutDoppler || g.cut_mode == kCutLorentz || g.W > 0.0;
+}
 
 // Per-line kernel parameters, as staged in shared memory.
 struct LineP {
@@ -287,26 +302,70 @@ __device__ __forceinline__ bool in_cut(long long k, double r, double W)
     return fabs(__dsub_rn((double)k, r)) <= W;
 }
 
-// Bin geometry of one line.  Returns false if no bin of the grid is inside.
-__device__ __forceinline__ bool line_geometry(double nu0, const GridD &g, int *i0_out,
-                                              double *r_out, int *lo_out, int *hi_out)
+// One line's cutting length in bins.  nocut: the whole grid.  Per-line
+// modes: W = (factor * Gamma) * inv_dnu with Gamma = nu0 * K_D (Doppler) or
+// the FP64 Lorentz half width A/(4 pi c) + gamma (T_ref/T)^n P/P_ref, in the
+// operation order of the oracle's definition.  Wi, Wf: the FP32 split of W
+// (Wi = -1 when W >= 2^30: no fast path).
+struct CutW {
+    bool nocut;
+    double W;
+    int Wi;
+    float Wf;
+};
+
+__device__ __forceinline__ CutW line_cut(const Prob &p, const GridD &g, int64_t l, double nu0)
+{
+    CutW c;
+    if (g.cut_mode == kCutDoppler || g.cut_mode == kCutLorentz) {
+        double G;
+        if (g.cut_mode == kCutDoppler) {
+            G = __dmul_rn(nu0, p.K_D);
+        } else {
+            const double nat = p.A ? __ddiv_rn((double)p.A[l], 4.0 * kPI * kC) : 0.0;
+            G = __dadd_rn(nat, __dmul_rn(__dmul_rn((double)p.gamma[l], pow(p.tratio, (double)p.n_T[l])),
+                                         p.press));
+        }
+        c.nocut = false;
+        c.W = __dmul_rn(__dmul_rn(g.cut_factor, G), g.inv_dnu);
+        if (c.W >= 0.0 && c.W < 1073741824.0) {
+            c.Wi = (int)floor(c.W);
+            c.Wf = (float)__dsub_rn(c.W, (double)c.Wi);
+        } else {
+            c.Wi = -1;
+            c.Wf = 0.0f;
+        }
+    } else {
+        c.nocut = !(g.W > 0.0);
+        c.W = g.W;
+        c.Wi = g.Wi;
+        c.Wf = g.Wf;
+    }
+    return c;
+}
+
+// Bin geometry of one line with cutting length W bins (nocut: the whole
+// grid).  Returns false if no bin of the grid is inside.
+__device__ __forceinline__ bool line_geometry_w(double nu0, const GridD &g, bool nocut, double W,
+                                                int *i0_out, double *r_out, int *lo_out,
+                                                int *hi_out)
 {
     double u = __dmul_rn(__dsub_rn(nu0, g.nu_min), g.inv_dnu);
     double f = floor(u);
     double r = __dsub_rn(u, f);
     long long i0 = (long long)f;
     long long lo, hi;
-    if (g.W <= 0.0) {
+    if (nocut) {
         lo = 0;
         hi = g.nbins - 1;
     } else {
-        long long kh = (long long)floor(__dadd_rn(r, g.W));
-        long long kl = (long long)ceil(__dsub_rn(r, g.W));
+        long long kh = (long long)floor(__dadd_rn(r, W));
+        long long kl = (long long)ceil(__dsub_rn(r, W));
         // walk to the exact predicate boundary (at most a step or two)
-        for (int it = 0; it < 4 && in_cut(kh + 1, r, g.W); ++it) ++kh;
-        for (int it = 0; it < 4 && !in_cut(kh, r, g.W) && kh >= kl; ++it) --kh;
-        for (int it = 0; it < 4 && in_cut(kl - 1, r, g.W); ++it) --kl;
-        for (int it = 0; it < 4 && !in_cut(kl, r, g.W) && kl <= kh; ++it) ++kl;
+        for (int it = 0; it < 4 && in_cut(kh + 1, r, W); ++it) ++kh;
+        for (int it = 0; it < 4 && !in_cut(kh, r, W) && kh >= kl; ++it) --kh;
+        for (int it = 0; it < 4 && in_cut(kl - 1, r, W); ++it) --kl;
+        for (int it = 0; it < 4 && !in_cut(kl, r, W) && kl <= kh; ++it) ++kl;
         lo = i0 + kl;
         hi = i0 + kh;
         if (lo < 0) lo = 0;
@@ -327,6 +386,13 @@ __device__ __forceinline__ bool line_geometry(double nu0, const GridD &g, int *i
     return true;
 }
 
+// The grid's fixed cut (or none).
+__device__ __forceinline__ bool line_geometry(double nu0, const GridD &g, int *i0_out,
+                                              double *r_out, int *lo_out, int *hi_out)
+{
+    return line_geometry_w(nu0, g, !(g.W > 0.0), g.W, i0_out, r_out, lo_out, hi_out);
+}
+
 // Bin geometry for the FP32 kernels, with as little FP64 arithmetic as the
 // exact cut decision allows (FP64 throughput is a small fraction of FP32).
 // u, i0 = floor(u) and r = u - i0 are the FP64 values of line_geometry.  The
@@ -337,8 +403,9 @@ __device__ __forceinline__ bool line_geometry(double nu0, const GridD &g, int *i
 // those lie more than 1e-5 from an integer; otherwise (and for W >= 2^30)
 // from line_geometry's exact FP64 walk.  Also returns the nearest bin c and
 // the offset rn in [-1/2, 1/2] (see nearest_bin) as a float.
-__device__ __forceinline__ bool line_geometry_f32(double nu0, const GridD &g, int *c_out,
-                                                  float *rn_out, int *lo_out, int *hi_out)
+__device__ __forceinline__ bool line_geometry_f32(double nu0, const GridD &g, const CutW &cw,
+                                                  int *c_out, float *rn_out, int *lo_out,
+                                                  int *hi_out)
 {
     const double u = __dmul_rn(__dsub_rn(nu0, g.nu_min), g.inv_dnu);
     const double f = floor(u);
@@ -347,23 +414,23 @@ __device__ __forceinline__ bool line_geometry_f32(double nu0, const GridD &g, in
     long long lo, hi;
     const long long i0 = (long long)f;
     bool exact = true;
-    if (g.W <= 0.0) {
+    if (cw.nocut) {
         lo = 0;
         hi = g.nbins - 1;
         exact = false;
-    } else if (g.Wi >= 0) {
-        const float sh = rf + g.Wf, sl = rf - g.Wf;
+    } else if (cw.Wi >= 0) {
+        const float sh = rf + cw.Wf, sl = rf - cw.Wf;
         const float th = sh - rintf(sh), tl = sl - rintf(sl);
         if (fabsf(th) > 1e-5f && fabsf(tl) > 1e-5f) {
-            hi = i0 + g.Wi + (long long)floorf(sh);
-            lo = i0 - g.Wi + (long long)ceilf(sl);
+            hi = i0 + cw.Wi + (long long)floorf(sh);
+            lo = i0 - cw.Wi + (long long)ceilf(sl);
             exact = false;
         }
     }
     if (exact) {
         int i0e, loe, hie;
         double re;
-        const bool any = line_geometry(nu0, g, &i0e, &re, &loe, &hie);
+        const bool any = line_geometry_w(nu0, g, cw.nocut, cw.W, &i0e, &re, &loe, &hie);
         lo = any ? loe : 1;
         hi = any ? hie : 0;
     } else {

@@ -19,9 +19,10 @@ HK_OK, HK_EINVAL, HK_ENOMEM, HK_ECUDA, HK_ETIMEOUT, HK_ENOTSUP, HK_ERANGE, HK_ES
 HK_NOALLOC_SCRATCH_BYTES = 16 << 20
 HK_S_REF, HK_S_EINSTEIN_A = 0, 1
 HK_FP32C, HK_FP64 = 0, 1
-HK_CUT_FIXED, HK_CUT_NONE = 0, 1
+HK_CUT_FIXED, HK_CUT_NONE, HK_CUT_DOPPLER, HK_CUT_LORENTZ = 0, 1, 2, 3
 HK_PER_GRAM = 1
 HK_SIGMA_F64 = 2
+HK_REMOVE_PLINTH = 4
 
 EXPORTS = ["hk_line_strength", "hk_widths", "hk_voigt_accumulate", "hk_cross_section",
            "hk_cross_section_batched", "hk_cross_section_backward", "hk_workspace_size",

@@ -151,6 +151,69 @@ def test_host_streamed_matches_oracle(hk):
     assert np.all(ge.numpy() == 0)
 
 
+def _oracle_ext(L, grid, T, P, cut, cut_mode, plinth):
+    return oracle.cross_section(L.as_oracle(), grid.astuple(), (T, P, float(Q(T)), QREF), cut,
+                                cut_mode=cut_mode, plinth=plinth)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_plinth_and_per_line_cuts(hk, prec):
+    """Doppler- and Lorentz-multiple cuts (Sect. 2.4.3 item 4) and plinth
+    removal (Sect. 2.1) on the config-0 list: pair totals equal the oracle's,
+    the same zero pattern, and parity.  With the plinth removed a bin near a
+    cut edge is a difference of two nearly equal values, so there the bar is
+    taken relative to the un-removed sigma (per bin 1e-4, L1 1e-5)."""
+    w = synth.config(0, scale=0.3)
+    L = w.species[0]
+    T, P = 1000.0, 1.0
+    grid = w.grid
+    D = hk.DeviceLines.from_host(L)
+    st = hk.make_state(T, P, float(Q(T)))
+    cases = [(hk.HK_CUT_FIXED, 25.0, True), (hk.HK_CUT_DOPPLER, 500.0, False),
+             (hk.HK_CUT_DOPPLER, 500.0, True), (hk.HK_CUT_LORENTZ, 150.0, False),
+             (hk.HK_CUT_LORENTZ, 150.0, True)]
+    for mode, cut, plinth in cases:
+        flags = (hk.HK_REMOVE_PLINTH if plinth else 0) | hk.HK_SIGMA_F64
+        opts = hk.make_opts(QREF, cut, prec, cut_mode=mode, flags=flags)
+        got = hk.hk_cross_section(D, hk.make_grid(*grid.astuple()), st, opts)
+        hk.hk_sync_status()
+        got = got.cpu().numpy()
+        ref = _oracle_ext(L, grid, T, P, cut, mode, plinth)
+        what = f"mode={mode} cut={cut} plinth={plinth} prec={prec}"
+        if mode != hk.HK_CUT_FIXED:
+            GLo = oracle.widths(L.nu0, L.gamma_ref, L.n_T, T, P, L.mass_amu)[1]
+            cl = oracle.line_cuts(L.nu0, GLo, mode, cut, T, L.mass_amu)
+            pairs = hk.hk_count_pairs(D, hk.make_grid(*grid.astuple()), st, opts)[0]
+            assert pairs == oracle.count_pairs_percut(L.nu0, cl, *grid.astuple()), what
+        # bins outside every cut are exactly zero on both sides (with the plinth
+        # removed an edge bin may also round to zero in FP32)
+        assert np.all(got[ref == 0] == 0) and (plinth or np.all(ref[got == 0] == 0)), what
+        if not plinth:
+            assert_sigma_close(got, ref, what)
+            continue
+        base = _oracle_ext(L, grid, T, P, cut, mode, False)
+        m = base > 1e-10 * base.max()
+        d = np.abs(got - ref)
+        assert np.max(d[m] / base[m]) <= 1e-4, what
+        assert d[m].sum() <= 1e-5 * base[m].sum(), what
+        # and the plinth-removed values themselves, where no cancellation occurs
+        far = m & (ref > 0.5 * base)
+        assert np.max(d[far] / ref[far]) <= 1e-4, what
+
+
+def test_backward_rejects_plinth_and_per_line_cuts(hk):
+    L = synth.make_lines(50, 0.0, 10.0, 3, 18.0)
+    D = hk.DeviceLines.from_host(L)
+    grid = hk.make_grid(0.0, 0.01, 1000)
+    g = torch.zeros((1, 1000), dtype=torch.float32, device="cuda")
+    st = [hk.make_state(500.0, 1.0, float(Q(500.0)), float(synth.dlnQ_dT(500.0)))]
+    for opts in (hk.make_opts(QREF, 5.0, cut_mode=hk.HK_CUT_DOPPLER),
+                 hk.make_opts(QREF, 2.0, flags=hk.HK_REMOVE_PLINTH)):
+        with pytest.raises(hk.HKError) as e:
+            hk.hk_cross_section_backward(D, grid, st, opts, g)
+        assert e.value.status == hk.HK_ENOTSUP
+
+
 def test_zero_lines_and_single_line(hk):
     L0 = synth.make_lines(0, 0, 10, 1, 18.0)
     grid = synth.Grid(0.0, 0.01, 1000)
