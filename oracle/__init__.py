@@ -50,6 +50,9 @@ def lib():
         _lib.hko_sigma_ext.argtypes = [i64, d, d, d, d, d, ctypes.c_int, ctypes.c_int,
                                        ctypes.c_double, ctypes.c_double, i64, ctypes.c_double,
                                        i64, i64, d, ctypes.c_int]
+        _lib.hko_sigma_prof.argtypes = [i64, d, d, d, d, d, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_double, ctypes.c_double, i64,
+                                        ctypes.c_double, i64, i64, d, ctypes.c_int]
         _lib.hko_backward.argtypes = [i64, d, d, d, d, d, d] + [ctypes.c_double] * 10 + [
             i64, ctypes.c_double, d, d, d, d, d, ctypes.c_int]
     return _lib
@@ -152,6 +155,7 @@ def count_pairs(nu0, nu_min, dnu, nbins, cut):
 
 
 CUT_FIXED, CUT_NONE, CUT_DOPPLER, CUT_LORENTZ = 0, 1, 2, 3
+PROFILE_VOIGT, PROFILE_LORENTZ, PROFILE_DOPPLER, PROFILE_BINNED_GAUSS = 0, 1, 2, 3
 
 
 def line_cuts(nu0, gammaL, mode, factor, T, mass_amu):
@@ -174,10 +178,11 @@ def count_pairs_percut(nu0, cut_l, nu_min, dnu, nbins):
 
 
 def sigma(nu0, S, alphaD, gammaL, nu_min, dnu, nbins, cut, bin_lo=0, bin_hi=None,
-          sorted_nu0=False, nthreads=0, cut_l=None, plinth=False):
+          sorted_nu0=False, nthreads=0, cut_l=None, plinth=False, profile=PROFILE_VOIGT):
     """sigma_i for bins [bin_lo, bin_hi): the direct FP64 sum of S * Re w / (alpha_D sqrt(pi)).
     cut_l: per-line cutting lengths (overrides `cut`); plinth: subtract each
-    line's value at its cutting length inside its cut (Sect. 2.1)."""
+    line's value at its cutting length inside its cut (Sect. 2.1); profile:
+    PROFILE_* (Voigt, Lorentzian, Doppler, binned Gaussian; Sect. 2.1)."""
     nu0 = _f64(nu0)
     n = nu0.size
     S = _f64(S, n)
@@ -187,14 +192,15 @@ def sigma(nu0, S, alphaD, gammaL, nu_min, dnu, nbins, cut, bin_lo=0, bin_hi=None
     if bin_hi is None:
         bin_hi = nbins
     out = np.zeros(max(bin_hi - bin_lo, 0))
-    lib().hko_sigma_ext(n, _d(nu0), _d(S), _d(aD), _d(GL), _d(cl) if cl is not None else None,
-                        int(bool(plinth)), int(bool(sorted_nu0)), nu_min, dnu, nbins, cut,
-                        bin_lo, bin_hi, _d(out), int(nthreads))
+    lib().hko_sigma_prof(n, _d(nu0), _d(S), _d(aD), _d(GL), _d(cl) if cl is not None else None,
+                         int(bool(plinth)), int(profile), int(bool(sorted_nu0)), nu_min, dnu,
+                         nbins, cut, bin_lo, bin_hi, _d(out), int(nthreads))
     return out
 
 
 def cross_section(lines, grid, state, cut, bin_lo=0, bin_hi=None, nthreads=0,
-                  T_ref=T_REF, P_ref=P_REF, per_gram=False, cut_mode=CUT_FIXED, plinth=False):
+                  T_ref=T_REF, P_ref=P_REF, per_gram=False, cut_mode=CUT_FIXED, plinth=False,
+                  profile=PROFILE_VOIGT):
     """Full path for one (T, P): S(T), widths, then the direct sum.
 
     ``lines``: mapping with nu0, E_low, gamma_ref, n_T and S_ref (s_mode 0) or
@@ -218,7 +224,7 @@ def cross_section(lines, grid, state, cut, bin_lo=0, bin_hi=None, nthreads=0,
         cut_l = line_cuts(lines["nu0"], GL, cut_mode, cut, T, lines["mass_amu"])
     return sigma(lines["nu0"], S, aD, GL, nu_min, dnu, nbins, cut, bin_lo, bin_hi,
                  sorted_nu0=bool(lines.get("sorted", False)), nthreads=nthreads, cut_l=cut_l,
-                 plinth=plinth)
+                 plinth=plinth, profile=profile)
 
 
 def backward(lines, grid, state, cut, grad_sigma, dL_dSref=None, dL_dgamma=None, nthreads=0,

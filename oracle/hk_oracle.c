@@ -359,10 +359,56 @@ int64_t hko_count_pairs(int64_t n, const double *nu0, double nu_min, double dnu,
  * line's cut the line's own value at the cutting length,
  * S Re w(cut_l / alpha_D + i y) / (alpha_D sqrt(pi)) (Sect. 2.1, "Removing
  * the Plinth"); a line without a cut has no plinth. */
+/* Line profiles (Sect. 2.1): sigma contribution S * phi of one line at
+ * offset d = nu - nu0 from its centre.
+ *   0 Voigt      phi = Re w(d / alpha_D + i y) / (alpha_D sqrt(pi))
+ *   1 Lorentz    phi = (Gamma_L / pi) / (d^2 + Gamma_L^2)
+ *   2 Doppler    phi = exp(-(d / alpha_D)^2) / (alpha_D sqrt(pi))
+ *   3 binned Gaussian integrated cross section (ExoCross): the Doppler profile
+ *                averaged over the bin [d - dnu/2, d + dnu/2],
+ *                phi = [erf((d + dnu/2)/alpha_D) - erf((d - dnu/2)/alpha_D)] / (2 dnu),
+ *                evaluated with erfc of positive arguments away from the centre
+ *                (erf(b) - erf(a) = erfc(a) - erfc(b)) so that no two values near
+ *                1 are subtracted. */
+static double profile_value(int profile, double S, double d, double aD, double GL, double dnu)
+{
+    switch (profile) {
+    case 1:
+        return S * (GL / O_PI) / (d * d + GL * GL);
+    case 2: {
+        double x = d / aD;
+        return S * exp(-x * x) / (aD * sqrt(O_PI));
+    }
+    case 3: {
+        double a = (fabs(d) - 0.5 * dnu) / aD, b = (fabs(d) + 0.5 * dnu) / aD;
+        double v = a >= 0.0 ? erfc(a) - erfc(b) : erf(b) + erf(-a);
+        return S * v / (2.0 * dnu);
+    }
+    default:
+        return S * creal(w_eval(d / aD, GL / aD)) / (aD * sqrt(O_PI));
+    }
+}
+
+void hko_sigma_prof(int64_t n, const double *nu0, const double *S, const double *alphaD,
+                    const double *gammaL, const double *cut_l, int plinth, int profile,
+                    int sorted_nu0, double nu_min, double dnu, int64_t nbins, double cut,
+                    int64_t bin_lo, int64_t bin_hi, double *sigma_out, int nthreads);
+
 void hko_sigma_ext(int64_t n, const double *nu0, const double *S, const double *alphaD,
                    const double *gammaL, const double *cut_l, int plinth, int sorted_nu0,
                    double nu_min, double dnu, int64_t nbins, double cut, int64_t bin_lo,
                    int64_t bin_hi, double *sigma_out, int nthreads)
+{
+    hko_sigma_prof(n, nu0, S, alphaD, gammaL, cut_l, plinth, 0, sorted_nu0, nu_min, dnu, nbins,
+                   cut, bin_lo, bin_hi, sigma_out, nthreads);
+}
+
+/* As hko_sigma_ext with a choice of line profile (see profile_value); the
+ * plinth is the profile's own value at the cutting length. */
+void hko_sigma_prof(int64_t n, const double *nu0, const double *S, const double *alphaD,
+                    const double *gammaL, const double *cut_l, int plinth, int profile,
+                    int sorted_nu0, double nu_min, double dnu, int64_t nbins, double cut,
+                    int64_t bin_lo, int64_t bin_hi, double *sigma_out, int nthreads)
 {
     const double inv_sqrt_pi = 1.0 / sqrt(O_PI);
     const double q = 1.0 / dnu;
@@ -417,10 +463,21 @@ void hko_sigma_ext(int64_t n, const double *nu0, const double *S, const double *
             bin_pos p = line_pos(nu0[l], nu_min, dnu);
             double y = gammaL[l] / alphaD[l];
             double amp = S[l] * inv_sqrt_pi / alphaD[l];
-            double h = (plinth && !nocut) ? amp * creal(w_eval(cl / alphaD[l], y)) : 0.0;
-            for (int64_t i = lo; i <= hi; ++i) {
-                double x = ((double)(i - p.i0) - p.r) * dnu / alphaD[l];
-                sigma_out[i - bin_lo] += amp * creal(w_eval(x, y)) - h;
+            if (profile == 0) {
+                double h = (plinth && !nocut) ? amp * creal(w_eval(cl / alphaD[l], y)) : 0.0;
+                for (int64_t i = lo; i <= hi; ++i) {
+                    double x = ((double)(i - p.i0) - p.r) * dnu / alphaD[l];
+                    sigma_out[i - bin_lo] += amp * creal(w_eval(x, y)) - h;
+                }
+            } else {
+                double h = (plinth && !nocut)
+                               ? profile_value(profile, S[l], cl, alphaD[l], gammaL[l], dnu)
+                               : 0.0;
+                for (int64_t i = lo; i <= hi; ++i) {
+                    double d = ((double)(i - p.i0) - p.r) * dnu;
+                    sigma_out[i - bin_lo] +=
+                        profile_value(profile, S[l], d, alphaD[l], gammaL[l], dnu) - h;
+                }
             }
         }
     }

@@ -300,6 +300,66 @@ def test_per_line_cuts_doppler_and_lorentz():
         assert oracle.count_pairs_percut(nu0, cuts, nu_min, dnu, nbins) == exact
 
 
+# -------------------------------------------------- line profiles (Sect. 2.1) --
+
+def _prof(profile, nu0, S, aD, GL, grid, cut, plinth=False):
+    return oracle.sigma(np.array([nu0]), np.array([S]), np.array([aD]), np.array([GL]), *grid,
+                        cut, profile=profile, plinth=plinth)
+
+
+def test_lorentz_and_doppler_profiles():
+    """Lorentzian: half maximum at Gamma_L, arctan area, and the Voigt's
+    alpha_D -> 0 limit (the Voigt path is pinned to mpmath).  Doppler: half
+    maximum at Gamma_D = sqrt(ln 2) alpha_D, erf area, and the Voigt at
+    Gamma_L = 0."""
+    dnu = 0.01
+    grid = (0.0, dnu, 20000)
+    nu0, S, GL = 100.0, 1.0, 0.25                          # on bin 10000; Gamma_L = 25 bins
+    lor = _prof(oracle.PROFILE_LORENTZ, nu0, S, 1e-3, GL, grid, 50.0)
+    assert abs(lor[10025] / lor[10000] - 0.5) < 1e-12
+    # the cut edges fall on bin centres: the point sum is the trapezoid rule plus
+    # half an end value at each edge
+    exact = 2 / math.pi * math.atan(50.0 / GL) + dnu * (GL / math.pi) / (50.0 ** 2 + GL ** 2)
+    assert abs(lor.sum() * dnu - exact) < 1e-8
+    voi = _prof(oracle.PROFILE_VOIGT, nu0, S, 1e-6, GL, grid, 50.0)
+    m = lor > 0
+    assert np.allclose(voi[m], lor[m], rtol=1e-9, atol=0)
+    aD = 0.3 / math.sqrt(math.log(2))                       # Gamma_D = 30 bins
+    dop = _prof(oracle.PROFILE_DOPPLER, nu0, S, aD, 0.0, grid, 5.0)
+    assert abs(dop[10030] / dop[10000] - 0.5) < 1e-12
+    assert abs(dop.sum() * dnu - math.erf(5.0 / aD)) < 1e-12
+    voi = _prof(oracle.PROFILE_VOIGT, nu0, S, aD, 0.0, grid, 5.0)
+    assert np.array_equal(voi, dop) or np.allclose(voi, dop, rtol=1e-14, atol=0)
+
+
+def test_binned_gaussian_telescopes_and_limits():
+    """Bin averages of the Gaussian telescope: the sum of sigma_i dnu over any
+    run of bins is S/2 [erf(right edge / alpha_D) - erf(left edge / alpha_D)]
+    (mpmath); for alpha_D >> dnu the binned values approach the point Doppler
+    profile to O((dnu / alpha_D)^2)."""
+    dnu = 0.05
+    grid = (0.0, dnu, 4000)
+    nu0, S, aD = 100.0123, 2.0, 0.037                        # narrower than a bin
+    b = _prof(oracle.PROFILE_BINNED_GAUSS, nu0, S, aD, 0.0, grid, 0.0)
+    for lo, hi in [(1990, 2010), (2000, 2001), (1998, 2000), (1000, 3000)]:
+        with mp.workdps(30):
+            left = mp.mpf(lo) * mp.mpf(dnu) - mp.mpf(dnu) / 2 - mp.mpf(nu0)
+            right = mp.mpf(hi) * mp.mpf(dnu) + mp.mpf(dnu) / 2 - mp.mpf(nu0)
+            ref = float(S / 2 * (mp.erf(right / aD) - mp.erf(left / aD)))
+        assert abs(b[lo:hi + 1].sum() * dnu - ref) <= 1e-13 * S, (lo, hi)
+    aD = 1.5                                                # 30 bins wide
+    b = _prof(oracle.PROFILE_BINNED_GAUSS, nu0, S, aD, 0.0, grid, 20.0)
+    d = _prof(oracle.PROFILE_DOPPLER, nu0, S, aD, 0.0, grid, 20.0)
+    m = d > 1e-6 * d.max()
+    # bin average of f = exp(-x^2), h = dnu/aD: f + (h^2/24) f2 + (h^4/1920) f4 + ...
+    # with f2/f = 4x^2 - 2 and f4/f = 16x^4 - 48x^2 + 12 (second, fourth derivatives)
+    x = (grid[0] + dnu * np.arange(grid[2]) - nu0) / aD
+    h = dnu / aD
+    X = x * x
+    pred = d * (1 + h ** 2 / 24 * (4 * X - 2) + h ** 4 / 1920 * (16 * X * X - 48 * X + 12))
+    assert np.max(np.abs(b[m] - pred[m]) / d[m]) < 2e-8
+
+
 # ------------------------------------------------------------ sigma: limits --
 
 def _single(nu0, S, aD, GL, grid, cut):
