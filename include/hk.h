@@ -88,6 +88,13 @@ extern "C" {
                             width in FP64 (a bin within one ulp of such a boundary may be
                             decided differently from a CPU evaluation: pow differs in its
                             last bit between math libraries) */
+/* line profile (Sect. 2.1: HELIOS-K offers four) */
+#define HK_PROFILE_VOIGT 0         /* Re w(x + iy) / (alpha_D sqrt(pi)) */
+#define HK_PROFILE_LORENTZ 1       /* (Gamma_L / pi) / ((nu - nu0)^2 + Gamma_L^2) */
+#define HK_PROFILE_DOPPLER 2       /* exp(-x^2) / (alpha_D sqrt(pi)) */
+#define HK_PROFILE_BINNED_GAUSS 3  /* the Doppler profile averaged over each bin
+                                      [nu_i - dnu/2, nu_i + dnu/2]: the "binned Gaussian
+                                      integrated cross section" of ExoCross */
 /* flags */
 #define HK_PER_GRAM 1u  /* divide S by the molecular mass in grams (Eq. S units) */
 #define HK_SIGMA_F64 2u /* HK_FP32C: write sigma as double instead of float.  The
@@ -142,9 +149,11 @@ typedef struct {
  * per-line half width (HK_CUT_DOPPLER, HK_CUT_LORENTZ; Sect. 2.4.3 item 4:
  * fixed length, Doppler or Lorentz half-width multiples).  precision:
  * HK_FP32C or HK_FP64.  flags: HK_PER_GRAM, HK_SIGMA_F64, HK_REMOVE_PLINTH.
- * The per-line cut modes and the plinth apply to every sigma entry point;
- * hk_voigt_accumulate takes its own fixed cut, and hk_cross_section_backward
- * supports HK_CUT_FIXED / HK_CUT_NONE without the plinth (else HK_ENOTSUP). */
+ * profile: HK_PROFILE_* (the plinth is the chosen profile's value at the
+ * cutting length).  The per-line cut modes, the plinth and the profiles
+ * apply to every sigma entry point; hk_voigt_accumulate takes its own fixed
+ * cut and the Voigt profile, and hk_cross_section_backward supports the Voigt
+ * profile with HK_CUT_FIXED / HK_CUT_NONE and no plinth (else HK_ENOTSUP). */
 typedef struct {
     double T_ref;
     double P_ref;
@@ -153,6 +162,7 @@ typedef struct {
     int cut_mode;
     int precision;
     unsigned flags;
+    int profile;
 } hk_opts;
 
 /* ---- entry points ------------------------------------------------------- */

@@ -181,11 +181,15 @@ static int check_opts(const hk_opts *o)
         return HK_EINVAL;
     if (o->precision != HK_FP32C && o->precision != HK_FP64) return HK_EINVAL;
     if (o->flags & ~(HK_PER_GRAM | HK_SIGMA_F64 | HK_REMOVE_PLINTH)) return HK_EINVAL;
+    if (o->profile < HK_PROFILE_VOIGT || o->profile > HK_PROFILE_BINNED_GAUSS) return HK_EINVAL;
     return HK_OK;
 }
 static_assert(kCutFixed == HK_CUT_FIXED && kCutNone == HK_CUT_NONE &&
                   kCutDoppler == HK_CUT_DOPPLER && kCutLorentz == HK_CUT_LORENTZ,
               "cut mode values");
+static_assert(kProfVoigt == HK_PROFILE_VOIGT && kProfLorentz == HK_PROFILE_LORENTZ &&
+                  kProfDoppler == HK_PROFILE_DOPPLER && kProfBinned == HK_PROFILE_BINNED_GAUSS,
+              "profile values");
 
 // The FP32 fast path of the cut bounds: W = Wi + Wf for 0 < W < 2^30.
 static void set_cut_split(GridD *d)
@@ -216,6 +220,7 @@ static GridD make_grid(const hk_grid *g, const hk_opts *o)
     d.cut_mode = d.W > 0.0 ? HK_CUT_FIXED : (perline ? mode : HK_CUT_NONE);
     d.cut_factor = perline ? o->cut : 0.0;
     d.plinth = (o && (o->flags & HK_REMOVE_PLINTH)) ? 1 : 0;
+    d.profile = o ? o->profile : HK_PROFILE_VOIGT;
     return d;
 }
 
@@ -232,6 +237,7 @@ static GridD make_grid_cut(const hk_grid *g, double cut)
     d.cut_mode = d.W > 0.0 ? HK_CUT_FIXED : HK_CUT_NONE;
     d.cut_factor = 0.0;
     d.plinth = 0;
+    d.profile = HK_PROFILE_VOIGT;
     return d;
 }
 
@@ -893,7 +899,7 @@ int hk_cross_section_backward(const hk_lines *lines, const hk_grid *grid, const 
     if (lines->n > 0 && (!dL_dSref || !dL_dgamma_ref)) return HK_EINVAL;
     if (lines->s_mode != HK_S_REF) return HK_ENOTSUP;
     if (opts->cut_mode == HK_CUT_DOPPLER || opts->cut_mode == HK_CUT_LORENTZ ||
-        (opts->flags & HK_REMOVE_PLINTH))
+        (opts->flags & HK_REMOVE_PLINTH) || opts->profile != HK_PROFILE_VOIGT)
         return HK_ENOTSUP;
     for (int k = 0; k < nTP; ++k)
         if ((rc = check_state(&TP[k]))) return rc;

@@ -53,12 +53,23 @@ template <typename R> struct LineT {
 // centre falls between bins never reaches its peak, so the peak is not used.
 // Re w(x, y) <= min(1, exp(-x^2) + y / (sqrt(pi) x^2)) bounds it within a
 // small factor, which is all the exponent needs.
-__device__ __forceinline__ int sampled_peak_exp2(float x_n, float y)
+// The other profiles: Lorentz (y/sqrt(pi)) / (X + y^2) exactly, Doppler
+// exp(-X) exactly, binned Gaussian at most min(1, sqrt(pi)/b).
+__device__ __forceinline__ int sampled_peak_exp2(float x_n, float y, int profile, float b)
 {
     float X = x_n * x_n;
-    float B = expf(-X) + (float)kInvSqrtPi * y / X;  // X = 0 gives +inf -> 1
-    B = fminf(B, 1.0f);
-    return B > 0.0f ? ilogbf(B) : INT_MIN / 2;
+    float B;
+    if (profile == kProfLorentz) {
+        B = (float)kInvSqrtPi * y / (X + y * y);
+    } else if (profile == kProfDoppler) {
+        B = expf(-X);
+    } else if (profile == kProfBinned) {
+        B = fminf(1.0f, (float)(1.0 / kInvSqrtPi) / b);
+    } else {
+        B = expf(-X) + (float)kInvSqrtPi * y / X;  // X = 0 gives +inf -> 1
+        B = fminf(B, 1.0f);
+    }
+    return B > 0.0f && B < INFINITY ? ilogbf(B) : INT_MIN / 2;
 }
 
 __global__ void k_scale_prepass(const Prob *__restrict__ probs, int nprob, GridD g)
@@ -80,13 +91,13 @@ __global__ void k_scale_prepass(const Prob *__restrict__ probs, int nprob, GridD
         if (pr.pre) {
             double v = pr.S_pre[l] * (double)pr.aDinv_pre[l] * kInvSqrtPi;
             float b = (float)g.dnu * pr.aDinv_pre[l];
-            e = v > 0.0 ? ilogb(v) + sampled_peak_exp2(rn * b, pr.y_pre[l]) : INT_MIN;
+            e = v > 0.0 ? ilogb(v) + sampled_peak_exp2(rn * b, pr.y_pre[l], kProfVoigt, b) : INT_MIN;
         } else {
             float P, aDinv, y;
             int e2;
             line_strength_f32(pr, l, &P, &e2, &aDinv, &y);
             float b = (float)g.dnu * aDinv;
-            e = P > 0.0f ? ilogbf(P) + e2 + sampled_peak_exp2(rn * b, y) : INT_MIN;
+            e = P > 0.0f ? ilogbf(P) + e2 + sampled_peak_exp2(rn * b, y, g.profile, b) : INT_MIN;
         }
         emax = max(emax, e);
     }
@@ -235,7 +246,8 @@ __device__ __forceinline__ void stage_line(const Prob &pr, const GridD &g, int64
         q.y = (R)y;
     }
     // the plinth: this line's value at its cutting length, x_cut = W b
-    q.h = (g.plinth && any && !cw.nocut) ? q.s * voigt_re<R>((R)cw.W * q.b, q.y) : R(0);
+    q.h = (g.plinth && any && !cw.nocut) ? q.s * profile_rel<R>(g.profile, (R)cw.W * q.b, q.y, q.b)
+                                         : R(0);
     *out = q;
     *nu_out = nu0;
 }
@@ -347,7 +359,9 @@ __global__ void __launch_bounds__(NTHREADS, 2)
                 for (int j = 0; j < BPT; ++j) {
                     const bool inr = (unsigned)(kk + 32 * j) <= span;
                     const R x = fma(kf0 + R(32 * j), q.b, -rb);
-                    const R v = pair_value<R>(x, y, Y, q.s, sy) - q.h;
+                    const R v = (g.profile == kProfVoigt ? pair_value<R>(x, y, Y, q.s, sy)
+                                                         : q.s * profile_rel<R>(g.profile, x, y, q.b)) -
+                                q.h;
                     acc[j] += inr ? v : R(0);
                 }
                 if (sizeof(R) == 4 && ++nsince == FLUSH) {

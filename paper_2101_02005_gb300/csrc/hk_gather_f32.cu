@@ -61,6 +61,9 @@ struct Smem {
     unsigned queue[NW][QCAP];
 };
 
+// Bands of the non-Voigt profiles (the Lorentzian is the one-node band itself)
+constexpr int kBandGauss = 10, kBandBinned = 11;
+
 constexpr float kTa = 0.27525512860841106f, kTb = 2.724744871391589f;   // 4-node tau
 constexpr float kWa = 2.0f * 0.4541241452319315f, kWb = 2.0f * 0.04587585476806851f;
 
@@ -132,7 +135,13 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
     q.sa = sy * kWa;
     q.sb = sy * kWb;
     // the plinth: this line's value at its cutting length, x_cut = W b
-    q.h = (g.plinth && any && !cw.nocut) ? sv * voigt_re<float>((float)cw.W * b, y) : 0.0f;
+    q.h = (g.plinth && any && !cw.nocut)
+              ? sv * profile_rel<float>(g.profile, (float)cw.W * b, y, b)
+              : 0.0f;
+    if (g.profile == kProfBinned) {          // sqrt(pi)/(2b) s and b/2 in the 2-node slots
+        q.sy2 = sv * (float)(0.5 / kInvSqrtPi) / b;
+        q.Yq = 0.5f * b;
+    }
     if (any) {
         q.gA = lo >> 5;
         q.gB = hi >> 5;
@@ -143,6 +152,10 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
     band_groups(1.5e6f, Y, b, q.rn, c, q.gA, q.gB, &q.L2, &q.R2);
     band_groups(2500.0f, Y, b, q.rn, c, q.L2, q.R2, &q.L4, &q.R4);
     band_groups(64.0f, Y, b, q.rn, c, q.L4, q.R4, &q.Lc, &q.Rc);
+    if (g.profile == kProfLorentz) {          // (y/sqrt(pi)) s / r2 on every bin: all one-node
+        q.L2 = q.L4 = q.Lc = q.gB + 1;
+        q.R2 = q.R4 = q.Rc = q.gB;
+    }
     *out = q;
 }
 
@@ -154,7 +167,12 @@ template <int BAND> __device__ __forceinline__ float pair_raw(const Rec &q, floa
     const float r2 = X + q.Y;
     // one hardware reciprocal and a multiply, within 2 ulp while the divisor
     // is below 2^126 (gh1 beyond that gives 0, far below any sum)
-    if (BAND == kBandGH1) {
+    if (BAND == kBandGauss) {
+        return q.s * exp2f(-X * 1.4426950408889634f);
+    } else if (BAND == kBandBinned) {
+        const float ax = fabsf(x), a = ax - q.Yq, c = ax + q.Yq;
+        return q.sy2 * (a >= 0.0f ? erfcf(a) - erfcf(c) : erff(c) + erff(-a));
+    } else if (BAND == kBandGH1) {
         return q.sy * rcp_ftz(r2);
     } else if (BAND == kBandGH2) {          // |z^2 - 1/2|^2 = r2^2 - X + Y + 1/4
         const float d = fmaf(r2, r2, q.Yq - X);
@@ -167,8 +185,10 @@ template <int BAND> __device__ __forceinline__ float pair_raw(const Rec &q, floa
 }
 
 // Launch variants V: bit 1 peels the edge groups (wide lines), bit 2 removes
-// the plinth (every in-range pair less the line's value at its cut).
-constexpr int kVPeel = 1, kVPlinth = 2;
+// the plinth (every in-range pair less the line's value at its cut), bits 4
+// and 8 select the Doppler and binned-Gaussian profiles (one formula for all
+// bins of a line; Voigt and Lorentzian run the banded sweeps).
+constexpr int kVPeel = 1, kVPlinth = 2, kVDoppler = 4, kVBinned = 8;
 
 template <int BAND, int V> __device__ __forceinline__ float pair_f(const Rec &q, float kf)
 {
@@ -301,6 +321,14 @@ __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1
     const int ga = max(q.gA, tg0), gb = min(q.gB, tg1);
     if (ga > gb) return;  // warp-uniform
     const int kfc = lane - q.c;
+    if (V & kVDoppler) {
+        sweep<kBandGauss, V>(q, q.gA, q.gB, ga, gb, tg0, base, kfc, lane);
+        return;
+    }
+    if (V & kVBinned) {
+        sweep<kBandBinned, V>(q, q.gA, q.gB, ga, gb, tg0, base, kfc, lane);
+        return;
+    }
     sweep<kBandGH1, V>(q, q.gA, q.L2 - 1, ga, gb, tg0, base, kfc, lane);
     sweep<kBandGH2, V>(q, q.L2, q.L4 - 1, ga, gb, tg0, base, kfc, lane);
     sweep<kBandGH4, V>(q, q.L4, q.Lc - 1, ga, gb, tg0, base, kfc, lane);
@@ -454,8 +482,16 @@ int gather_f32_launch(const Prob *probs_d, const GridD &g, int64_t ntiles, int64
                       int lmax, unsigned long long *counter, cudaStream_t st, int num_sms)
 {
     const bool wide = g.W <= 0.0 || 2.0 * g.W + 1.0 >= kPeelBins;
-    const int v = (wide ? f32g::kVPeel : 0) | (g.plinth && has_cut(g) ? f32g::kVPlinth : 0);
+    int v = (wide ? f32g::kVPeel : 0) | (g.plinth && has_cut(g) ? f32g::kVPlinth : 0);
+    if (g.profile == kProfDoppler) v = f32g::kVPeel | f32g::kVPlinth | f32g::kVDoppler;
+    if (g.profile == kProfBinned) v = f32g::kVPeel | f32g::kVPlinth | f32g::kVBinned;
     switch (v) {
+    case f32g::kVPeel | f32g::kVPlinth | f32g::kVDoppler:
+        return launch_variant<f32g::kVPeel | f32g::kVPlinth | f32g::kVDoppler>(
+            probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter, st, num_sms);
+    case f32g::kVPeel | f32g::kVPlinth | f32g::kVBinned:
+        return launch_variant<f32g::kVPeel | f32g::kVPlinth | f32g::kVBinned>(
+            probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter, st, num_sms);
     case 0:
         return launch_variant<0>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
                                  counter, st, num_sms);

@@ -23,6 +23,10 @@ constexpr double kInvSqrtPi = 0.5641895835477563;
 constexpr double kInvPi = 0.3183098861837907;
 constexpr double kInvLn2 = 1.4426950408889634;
 
+// Cut modes and line profiles (the values of HK_CUT_* and HK_PROFILE_* in hk.h).
+constexpr int kCutFixed = 0, kCutNone = 1, kCutDoppler = 2, kCutLorentz = 3;
+constexpr int kProfVoigt = 0, kProfLorentz = 1, kProfDoppler = 2, kProfBinned = 3;
+
 // ---- Faddeeva function: banded evaluation of Re w(x + iy), y >= 0 ----------
 //
 // The a-u plane split of Sect. 2.2.3 (Table regions) is prior art; the bands
@@ -223,6 +227,31 @@ template <typename R> __device__ __forceinline__ R voigt_re(R x, R y)
     return core_re<R>(x, y);
 }
 
+// A line's value at offset x (in alpha_D; y = Gamma_L / alpha_D, b = dnu /
+// alpha_D) relative to s = S alpha_D^-1 / sqrt(pi), for each profile of
+// Sect. 2.1: Voigt Re w(x + iy); Lorentz (y / sqrt(pi)) / (x^2 + y^2);
+// Doppler exp(-x^2); binned Gaussian (the Doppler profile averaged over the
+// bin) sqrt(pi)/(2b) [erf(|x| + b/2) - erf(|x| - b/2)], as a difference of
+// erfc of positive arguments away from the centre so that no two values near
+// 1 are subtracted.
+template <typename R> __device__ __forceinline__ R profile_rel(int profile, R x, R y, R b)
+{
+    switch (profile) {
+    case kProfLorentz:
+        return R(kInvSqrtPi) * y / (x * x + y * y);
+    case kProfDoppler:
+        return exp(-x * x);
+    case kProfBinned: {
+        const R ax = x < R(0) ? -x : x, hb = R(0.5) * b;
+        const R a = ax - hb, c = ax + hb;
+        const R v = a >= R(0) ? erfc(a) - erfc(c) : erf(c) + erf(-a);
+        return R(0.5 / kInvSqrtPi) / b * v;
+    }
+    default:
+        return voigt_re<R>(x, y);
+    }
+}
+
 // ---- problem descriptors ----------------------------------------------------
 
 // One sigma array to compute: one species at one (T, P), scalars prepared on
@@ -264,9 +293,6 @@ struct Prob {
 constexpr unsigned kStatusRange = 1u;    // a float output overflowed
 constexpr unsigned kStatusTimeout = 2u;  // a bounded device wait gave up
 
-// Cut modes (the values of HK_CUT_* in hk.h).
-constexpr int kCutFixed = 0, kCutNone = 1, kCutDoppler = 2, kCutLorentz = 3;
-
 struct GridD {
     double nu_min, dnu, inv_dnu;
     double W;                   // fixed cut / dnu (as cut * inv_dnu); <= 0: no fixed cut
@@ -277,6 +303,7 @@ struct GridD {
     int cut_mode;               // kCut*: per-line modes take cut_factor times a half width
     double cut_factor;
     int plinth;                 // subtract each line's value at its cutting length
+    int profile;                // kProf*
 };
 
 // Whether the lines have a cut at all (fixed or per line).

@@ -23,6 +23,7 @@ HK_CUT_FIXED, HK_CUT_NONE, HK_CUT_DOPPLER, HK_CUT_LORENTZ = 0, 1, 2, 3
 HK_PER_GRAM = 1
 HK_SIGMA_F64 = 2
 HK_REMOVE_PLINTH = 4
+HK_PROFILE_VOIGT, HK_PROFILE_LORENTZ, HK_PROFILE_DOPPLER, HK_PROFILE_BINNED_GAUSS = 0, 1, 2, 3
 
 EXPORTS = ["hk_line_strength", "hk_widths", "hk_voigt_accumulate", "hk_cross_section",
            "hk_cross_section_batched", "hk_cross_section_backward", "hk_workspace_size",
@@ -50,7 +51,7 @@ class hk_state(ctypes.Structure):
 class hk_opts(ctypes.Structure):
     _fields_ = [("T_ref", ctypes.c_double), ("P_ref", ctypes.c_double),
                 ("Q_Tref", ctypes.c_double), ("cut", ctypes.c_double), ("cut_mode", ctypes.c_int),
-                ("precision", ctypes.c_int), ("flags", ctypes.c_uint)]
+                ("precision", ctypes.c_int), ("flags", ctypes.c_uint), ("profile", ctypes.c_int)]
 
 
 class HKError(RuntimeError):
@@ -190,11 +191,11 @@ def make_state(T, P, Q_T, dlnQ_dT=0.0) -> hk_state:
 
 
 def make_opts(Q_Tref, cut, precision=HK_FP32C, T_ref=296.0, P_ref=1.0, cut_mode=None,
-              flags=0) -> hk_opts:
+              flags=0, profile=HK_PROFILE_VOIGT) -> hk_opts:
     if cut_mode is None:
         cut_mode = HK_CUT_FIXED if cut > 0 else HK_CUT_NONE
     return hk_opts(float(T_ref), float(P_ref), float(Q_Tref), float(cut), int(cut_mode),
-                   int(precision), int(flags))
+                   int(precision), int(flags), int(profile))
 
 
 def sigma_dtype(opts: hk_opts):

@@ -201,6 +201,44 @@ def test_plinth_and_per_line_cuts(hk, prec):
         assert np.max(d[far] / ref[far]) <= 1e-4, what
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_line_profiles(hk, prec):
+    """Lorentzian, Doppler and binned-Gaussian profiles (Sect. 2.1) on the
+    config-0 list, with and without the plinth and with a Doppler-multiple
+    cut, against the oracle (same bars as test_plinth_and_per_line_cuts)."""
+    w = synth.config(0, scale=0.3)
+    L = w.species[0]
+    T, P = 1000.0, 1.0
+    grid = w.grid
+    D = hk.DeviceLines.from_host(L)
+    st = hk.make_state(T, P, float(Q(T)))
+    cases = []
+    for prof in (hk.HK_PROFILE_LORENTZ, hk.HK_PROFILE_DOPPLER, hk.HK_PROFILE_BINNED_GAUSS):
+        cases += [(prof, hk.HK_CUT_FIXED, 25.0, False), (prof, hk.HK_CUT_FIXED, 25.0, True)]
+    cases += [(hk.HK_PROFILE_DOPPLER, hk.HK_CUT_DOPPLER, 40.0, True)]
+    for prof, mode, cut, plinth in cases:
+        flags = (hk.HK_REMOVE_PLINTH if plinth else 0) | hk.HK_SIGMA_F64
+        opts = hk.make_opts(QREF, cut, prec, cut_mode=mode, flags=flags, profile=prof)
+        got = hk.hk_cross_section(D, hk.make_grid(*grid.astuple()), st, opts)
+        hk.hk_sync_status()
+        got = got.cpu().numpy()
+        args = (L.as_oracle(), grid.astuple(), (T, P, float(Q(T)), QREF), cut)
+        ref = oracle.cross_section(*args, cut_mode=mode, plinth=plinth, profile=prof)
+        what = f"profile={prof} mode={mode} plinth={plinth} prec={prec}"
+        # outside every cut zero; far tails (exp(-x^2) ~ 1e-300) may underflow on one
+        # side only, far below the mask
+        assert np.all(np.isfinite(got)), what
+        assert np.all(np.abs(got[ref == 0]) <= 1e-14 * ref.max()), what
+        if not plinth:
+            assert_sigma_close(got, ref, what)
+            continue
+        base = oracle.cross_section(*args, cut_mode=mode, plinth=False, profile=prof)
+        m = base > 1e-10 * base.max()
+        d = np.abs(got - ref)
+        assert np.max(d[m] / base[m]) <= 1e-4, what
+        assert d[m].sum() <= 1e-5 * base[m].sum(), what
+
+
 def test_backward_rejects_plinth_and_per_line_cuts(hk):
     L = synth.make_lines(50, 0.0, 10.0, 3, 18.0)
     D = hk.DeviceLines.from_host(L)
@@ -208,7 +246,8 @@ def test_backward_rejects_plinth_and_per_line_cuts(hk):
     g = torch.zeros((1, 1000), dtype=torch.float32, device="cuda")
     st = [hk.make_state(500.0, 1.0, float(Q(500.0)), float(synth.dlnQ_dT(500.0)))]
     for opts in (hk.make_opts(QREF, 5.0, cut_mode=hk.HK_CUT_DOPPLER),
-                 hk.make_opts(QREF, 2.0, flags=hk.HK_REMOVE_PLINTH)):
+                 hk.make_opts(QREF, 2.0, flags=hk.HK_REMOVE_PLINTH),
+                 hk.make_opts(QREF, 2.0, profile=hk.HK_PROFILE_LORENTZ)):
         with pytest.raises(hk.HKError) as e:
             hk.hk_cross_section_backward(D, grid, st, opts, g)
         assert e.value.status == hk.HK_ENOTSUP
