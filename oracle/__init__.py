@@ -53,6 +53,8 @@ def lib():
         _lib.hko_sigma_prof.argtypes = [i64, d, d, d, d, d, ctypes.c_int, ctypes.c_int,
                                         ctypes.c_int, ctypes.c_double, ctypes.c_double, i64,
                                         ctypes.c_double, i64, i64, d, ctypes.c_int]
+        _lib.hko_widths_hitran.argtypes = [i64, d, d, d, d, d] + [ctypes.c_double] * 6 + [d, d]
+        _lib.hko_shift.argtypes = [i64, d, d, ctypes.c_double, ctypes.c_double, d]
         _lib.hko_backward.argtypes = [i64, d, d, d, d, d, d] + [ctypes.c_double] * 10 + [
             i64, ctypes.c_double, d, d, d, d, d, ctypes.c_int]
     return _lib
@@ -137,6 +139,27 @@ def widths(nu0, gamma_ref, n_T, T, P, mass_amu, A=None, T_ref=T_REF, P_ref=P_REF
     return aD, GL
 
 
+def widths_hitran(nu0, gamma_air, gamma_self, n_T, T, P, P_self, mass_amu, A=None, T_ref=T_REF,
+                  P_ref=P_REF):
+    """(alpha_D, Gamma_L) with the HITRAN air/self-broadened Lorentz width (Eq. gammaL)."""
+    nu0 = _f64(nu0)
+    n = nu0.size
+    ga, gs, nT = _f64(gamma_air, n), _f64(gamma_self, n), _f64(n_T, n)
+    A = _f64(A, n) if A is not None else None
+    aD, GL = np.empty(n), np.empty(n)
+    lib().hko_widths_hitran(n, _d(nu0), _d(ga), _d(gs), _d(nT), _d(A) if A is not None else None,
+                            T, P, P_self, T_ref, P_ref, mass_amu, _d(aD), _d(GL))
+    return aD, GL
+
+
+def shift(nu0, delta, P, P_ref=P_REF):
+    """Pressure-shifted positions nu0 + delta P / P_ref."""
+    nu0 = _f64(nu0)
+    out = np.empty(nu0.size)
+    lib().hko_shift(nu0.size, _d(nu0), _d(_f64(delta, nu0.size)), P, P_ref, _d(out))
+    return out
+
+
 def line_ranges(nu0, nu_min, dnu, nbins, cut):
     """Inclusive bin range [lo, hi] of each line inside the cut (cut <= 0: all)."""
     nu0 = _f64(nu0)
@@ -200,7 +223,7 @@ def sigma(nu0, S, alphaD, gammaL, nu_min, dnu, nbins, cut, bin_lo=0, bin_hi=None
 
 def cross_section(lines, grid, state, cut, bin_lo=0, bin_hi=None, nthreads=0,
                   T_ref=T_REF, P_ref=P_REF, per_gram=False, cut_mode=CUT_FIXED, plinth=False,
-                  profile=PROFILE_VOIGT):
+                  profile=PROFILE_VOIGT, P_self=0.0):
     """Full path for one (T, P): S(T), widths, then the direct sum.
 
     ``lines``: mapping with nu0, E_low, gamma_ref, n_T and S_ref (s_mode 0) or
@@ -208,6 +231,9 @@ def cross_section(lines, grid, state, cut, bin_lo=0, bin_hi=None, nthreads=0,
     sorted.  ``grid``: (nu_min, dnu, nbins).  ``state``: (T, P, Q_T, Q_Tref).
     cut_mode CUT_DOPPLER / CUT_LORENTZ: ``cut`` is the factor of the per-line
     half width; CUT_NONE: no cut.  plinth: remove the plinth (Sect. 2.1).
+    HITRAN lists: ``gamma_self`` in ``lines`` selects the air/self width of
+    Eq. gammaL (gamma_ref is then gamma_air; P_self the self partial pressure),
+    ``delta`` the pressure shift of the positions.
     """
     nu_min, dnu, nbins = grid
     T, P, Q_T, Q_Tref = state[:4]
@@ -215,15 +241,25 @@ def cross_section(lines, grid, state, cut, bin_lo=0, bin_hi=None, nthreads=0,
     S = line_strength(lines["nu0"], lines["E_low"], T, Q_T, Q_Tref, lines["mass_amu"],
                       S_ref=lines.get("S_ref"), A=lines.get("A"), g_up=lines.get("g_up"),
                       s_mode=s_mode, T_ref=T_ref, per_gram=per_gram)
-    aD, GL = widths(lines["nu0"], lines["gamma_ref"], lines["n_T"], T, P, lines["mass_amu"],
-                    A=lines.get("A"), T_ref=T_ref, P_ref=P_ref)
+    if lines.get("gamma_self") is not None:
+        aD, GL = widths_hitran(lines["nu0"], lines["gamma_ref"], lines["gamma_self"],
+                               lines["n_T"], T, P, P_self, lines["mass_amu"], A=lines.get("A"),
+                               T_ref=T_ref, P_ref=P_ref)
+    else:
+        aD, GL = widths(lines["nu0"], lines["gamma_ref"], lines["n_T"], T, P, lines["mass_amu"],
+                        A=lines.get("A"), T_ref=T_ref, P_ref=P_ref)
+    pos = lines["nu0"]
+    sorted_pos = bool(lines.get("sorted", False))
+    if lines.get("delta") is not None:
+        pos = shift(lines["nu0"], lines["delta"], P, P_ref)
+        sorted_pos = False
     cut_l = None
     if cut_mode == CUT_NONE:
         cut = 0.0
     elif cut_mode in (CUT_DOPPLER, CUT_LORENTZ):
         cut_l = line_cuts(lines["nu0"], GL, cut_mode, cut, T, lines["mass_amu"])
-    return sigma(lines["nu0"], S, aD, GL, nu_min, dnu, nbins, cut, bin_lo, bin_hi,
-                 sorted_nu0=bool(lines.get("sorted", False)), nthreads=nthreads, cut_l=cut_l,
+    return sigma(pos, S, aD, GL, nu_min, dnu, nbins, cut, bin_lo, bin_hi,
+                 sorted_nu0=sorted_pos, nthreads=nthreads, cut_l=cut_l,
                  plinth=plinth, profile=profile)
 
 

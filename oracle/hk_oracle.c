@@ -225,6 +225,37 @@ void hko_widths(int64_t n, const double *nu0, const double *gamma_ref, const dou
     }
 }
 
+/* HITRAN Lorentz half width (Sect. 2.2, Eq. gammaL, air and self broadening):
+ * Gamma_L = A/(4 pi c) + (T/T_ref)^-n [gamma_air (P - P_self)/P_ref + gamma_self P_self/P_ref].
+ * alpha_D as hko_widths.  A may be NULL (A = 0). */
+void hko_widths_hitran(int64_t n, const double *nu0, const double *gamma_air,
+                       const double *gamma_self, const double *n_T, const double *A, double T,
+                       double P, double P_self, double T_ref, double P_ref, double mass_amu,
+                       double *alphaD_out, double *gammaL_out)
+{
+    const double m_g = mass_amu * O_AMU;
+#pragma omp parallel for schedule(static)
+    for (int64_t l = 0; l < n; ++l) {
+        alphaD_out[l] = nu0[l] / O_C * sqrt(2.0 * O_KB * T / m_g);
+        double nat = A ? A[l] / (4.0 * O_PI * O_C) : 0.0;
+        gammaL_out[l] = nat + pow(T / T_ref, -n_T[l]) * (gamma_air[l] * (P - P_self) / P_ref +
+                                                         gamma_self[l] * P_self / P_ref);
+    }
+}
+
+/* Pressure-shifted line positions (the shift delta of the HITRAN/HITEMP data,
+ * Table binary2, cm^-1 per unit of P_ref): nu0 + delta * (P / P_ref).  The
+ * shift moves the line; its strength and Doppler width keep the transition
+ * wavenumber nu0. */
+void hko_shift(int64_t n, const double *nu0, const double *delta, double P, double P_ref,
+               double *out)
+{
+    const double press = P / P_ref;
+#pragma omp parallel for schedule(static)
+    for (int64_t l = 0; l < n; ++l)
+        out[l] = nu0[l] + delta[l] * press;
+}
+
 /* ---- cut predicate ------------------------------------------------------ */
 
 typedef struct {

@@ -28,7 +28,7 @@ import numpy as np
 
 SEED_BASE = 2101020050
 _FIELDS = {"nu0": 1, "S_ref": 2, "E_low": 3, "gamma_ref": 4, "n_T": 5, "A": 6, "g_up": 7,
-           "counts": 8, "grad": 100}
+           "counts": 8, "gamma_self": 9, "delta": 10, "grad": 100}
 
 
 def stream(seed: int, fld: str) -> np.random.Generator:
@@ -81,6 +81,8 @@ class LineList:
     g_up: Optional[np.ndarray] = None  # f32 [n]
     s_mode: int = 0
     sorted: bool = True
+    gamma_self: Optional[np.ndarray] = None  # f32 [n], HITRAN self broadening (gamma_ref = air)
+    delta: Optional[np.ndarray] = None       # f32 [n], pressure shift, cm^-1 / P_ref
 
     @property
     def n(self) -> int:
@@ -93,13 +95,17 @@ class LineList:
             d["A"] = self.A
         if self.g_up is not None:
             d["g_up"] = self.g_up
+        if self.gamma_self is not None:
+            d["gamma_self"] = self.gamma_self
+        if self.delta is not None:
+            d["delta"] = self.delta
         return d
 
     def subset(self, idx) -> "LineList":
         f = lambda a: None if a is None else a[idx]
         return LineList(self.nu0[idx], self.S_ref[idx], self.E_low[idx], self.gamma_ref[idx],
                         self.n_T[idx], self.mass_amu, f(self.A), f(self.g_up), self.s_mode,
-                        self.sorted)
+                        self.sorted, f(self.gamma_self), f(self.delta))
 
 
 def make_lines(n: int, nu_lo: float, nu_hi: float, seed: int, mass_amu: float,
@@ -108,7 +114,7 @@ def make_lines(n: int, nu_lo: float, nu_hi: float, seed: int, mass_amu: float,
                nT_range: Tuple[float, float] = (0.3, 0.8),
                A_range: Optional[Tuple[float, float]] = None,
                windows: Optional[int] = None, window_sigma: float = 1.5,
-               sort: bool = True) -> LineList:
+               sort: bool = True, hitran: bool = False) -> LineList:
     """Draw a line list.  ``windows``: number of equal-width windows with
     log-normal line counts (None: one window)."""
     n = int(n)
@@ -154,7 +160,18 @@ def make_lines(n: int, nu_lo: float, nu_hi: float, seed: int, mass_amu: float,
         stream(seed, "A").random(dtype=f32, out=A)
         A *= f32(A_range[1] - A_range[0])
         A += f32(A_range[0])
-    return LineList(nu0, S_ref, E_low, gamma, n_T, float(mass_amu), A=A, sorted=bool(sort))
+    gs = dl = None
+    if hitran:   # HITRAN-like air/self widths and pressure shifts
+        gs = np.empty(n, f32)
+        stream(seed, "gamma_self").random(dtype=f32, out=gs)
+        gs *= f32(0.4)
+        gs += f32(0.1)
+        dl = np.empty(n, f32)
+        stream(seed, "delta").random(dtype=f32, out=dl)
+        dl *= f32(0.03)
+        dl -= f32(0.02)
+    return LineList(nu0, S_ref, E_low, gamma, n_T, float(mass_amu), A=A, sorted=bool(sort),
+                    gamma_self=gs, delta=dl)
 
 
 @dataclass

@@ -300,6 +300,41 @@ def test_per_line_cuts_doppler_and_lorentz():
         assert oracle.count_pairs_percut(nu0, cuts, nu_min, dnu, nbins) == exact
 
 
+# ----------------------------------- HITRAN broadening and pressure shift (Sect. 2.2) --
+
+def test_hitran_width_reduces_to_the_exomol_form():
+    """Eq. gammaL: with P_self = 0 it is the ExoMol form with gamma_air, with
+    P_self = P the ExoMol form with gamma_self, and it is affine in P_self."""
+    rng = np.random.default_rng(41)
+    n = 50
+    nu0 = rng.uniform(10, 3000, n)
+    ga, gs, nT = rng.uniform(0.01, 0.1, n), rng.uniform(0.1, 0.5, n), rng.uniform(0.3, 0.8, n)
+    A = rng.uniform(1e6, 1e8, n)
+    T, P, m = 700.0, 2.5, 18.0
+    _, e_air = oracle.widths(nu0, ga, nT, T, P, m, A=A)
+    _, e_self = oracle.widths(nu0, gs, nT, T, P, m, A=A)
+    aD, h0 = oracle.widths_hitran(nu0, ga, gs, nT, T, P, 0.0, m, A=A)
+    _, h1 = oracle.widths_hitran(nu0, ga, gs, nT, T, P, P, m, A=A)
+    _, hh = oracle.widths_hitran(nu0, ga, gs, nT, T, P, 0.5 * P, m, A=A)
+    assert np.allclose(h0, e_air, rtol=1e-14, atol=0) and np.allclose(h1, e_self, rtol=1e-14, atol=0)
+    assert np.allclose(hh, 0.5 * (h0 + h1), rtol=1e-14, atol=0)
+    assert np.array_equal(aD, oracle.widths(nu0, ga, nT, T, P, m)[0])
+
+
+def test_pressure_shift_translates_the_line():
+    """A shift delta P / P_ref of exactly k bins moves sigma by k bins and
+    changes nothing else (the strength and width keep nu0)."""
+    dnu = 0.125
+    grid = (0.0, dnu, 400)
+    L = dict(nu0=np.array([20.0625]), S_ref=np.array([1e-20]), E_low=np.array([500.0]),
+             gamma_ref=np.array([0.07]), n_T=np.array([0.6]), mass_amu=18.0, s_mode=0)
+    state = (800.0, 2.0, 0.1 * 800 ** 1.5, 0.1 * 296 ** 1.5)
+    base = oracle.cross_section(L, grid, state, 5.0)
+    Ls = dict(L, delta=np.array([0.375]))                  # 0.375 * 2 bar = 0.75 = 6 bins
+    shifted = oracle.cross_section(Ls, grid, state, 5.0)
+    assert np.array_equal(shifted[6:], base[:-6]) and np.all(shifted[:6] == 0)
+
+
 # -------------------------------------------------- line profiles (Sect. 2.1) --
 
 def _prof(profile, nu0, S, aD, GL, grid, cut, plinth=False):
