@@ -123,6 +123,13 @@ typedef struct {
     double mass_amu;         /* molecular mass, atomic mass units */
     int s_mode;              /* HK_S_REF or HK_S_EINSTEIN_A */
     int sorted;              /* 1 if nu0 is ascending */
+    const float *gamma_self; /* [n] or NULL.  Non-NULL: HITRAN widths (Sect. 2.2, Eq.
+                                gammaL), gamma_ref is then gamma_air and
+                                Gamma_L = A/(4 pi c) + (T_ref/T)^n [gamma_air (P - P_self)
+                                + gamma_self P_self] / P_ref */
+    const float *delta;      /* [n] or NULL: pressure shift (Table binary2), cm^-1 per
+                                P_ref; the line sits at nu0 + delta P / P_ref (FP64), its
+                                strength and Doppler width keep nu0.  Sorting is by nu0 */
 } hk_lines;
 
 /* Uniform wavenumber grid nu_i = nu_min + i * dnu, 0 <= i < nbins
@@ -141,6 +148,7 @@ typedef struct {
     double P;
     double Q_T;
     double dlnQ_dT;
+    double P_self;           /* self partial pressure (HITRAN widths only), 0 <= P_self */
 } hk_state;
 
 /* Options.  T_ref, P_ref, Q_Tref: reference state of S_ref and gamma_ref
@@ -153,7 +161,8 @@ typedef struct {
  * cutting length).  The per-line cut modes, the plinth and the profiles
  * apply to every sigma entry point; hk_voigt_accumulate takes its own fixed
  * cut and the Voigt profile, and hk_cross_section_backward supports the Voigt
- * profile with HK_CUT_FIXED / HK_CUT_NONE and no plinth (else HK_ENOTSUP). */
+ * profile with HK_CUT_FIXED / HK_CUT_NONE, no plinth and lines without
+ * gamma_self or delta (else HK_ENOTSUP). */
 typedef struct {
     double T_ref;
     double P_ref;

@@ -164,7 +164,7 @@ static int check_grid(const hk_grid *g)
 static int check_state(const hk_state *s)
 {
     if (!s || !finite_pos(s->T) || !std::isfinite(s->P) || s->P < 0 || !finite_pos(s->Q_T) ||
-        !std::isfinite(s->dlnQ_dT))
+        !std::isfinite(s->dlnQ_dT) || !std::isfinite(s->P_self) || s->P_self < 0)
         return HK_EINVAL;
     return HK_OK;
 }
@@ -252,6 +252,8 @@ static void set_f32_scalars(Prob *p)
     p->log2_tratio_f = (float)p->log2_tratio;
     p->press_f = (float)p->press;
     p->nat_coef_f = (float)p->nat_coef;
+    p->press_air_f = (float)p->press_air;
+    p->press_self_f = (float)p->press_self;
     p->K2_hi = (float)p->K2;
     p->K2_lo = (float)(p->K2 - (double)p->K2_hi);
 }
@@ -289,6 +291,10 @@ static Prob make_prob(const hk_lines *L, const hk_state *s, const hk_opts *o)
     p.inv_Pref = 1.0 / o->P_ref;
     p.nat_coef = 1.0 / (4.0 * kPI * kC);
     p.tratio = o->T_ref / T;
+    p.gamma_self = L->gamma_self;
+    p.delta = L->delta;
+    p.press_air = (s->P - s->P_self) / o->P_ref;
+    p.press_self = s->P_self / o->P_ref;
     // the same operations, in the same order, as the oracle's Doppler cut width
     p.K_D = std::sqrt(0.6931471805599453) * std::sqrt(2.0 * kKB * T / m_g) / kC;
     set_f32_scalars(&p);
@@ -330,7 +336,7 @@ __global__ void k_sort_keys(const double *nu0, int64_t n, unsigned long long *ke
 
 __global__ void k_gather_fields(const hk_lines L, const int64_t *perm, int64_t n, double *nu0,
                                 float *S_ref, float *A, float *g_up, float *E_low, float *gamma,
-                                float *n_T)
+                                float *n_T, float *gamma_self, float *delta)
 {
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < n;
          l += (int64_t)gridDim.x * blockDim.x) {
@@ -342,6 +348,8 @@ __global__ void k_gather_fields(const hk_lines L, const int64_t *perm, int64_t n
         E_low[l] = L.E_low[s];
         gamma[l] = L.gamma_ref[s];
         n_T[l] = L.n_T[s];
+        if (L.gamma_self) gamma_self[l] = L.gamma_self[s];
+        if (L.delta) delta[l] = L.delta[s];
     }
 }
 
@@ -355,7 +363,7 @@ size_t sort_bytes(int64_t n, size_t *cub_bytes)
                                     (unsigned long long *)nullptr, (const int64_t *)nullptr,
                                     (int64_t *)nullptr, (int64_t)n, 0, 64, (cudaStream_t)0);
     *cub_bytes = tb;
-    return al(tb) + 2 * al(n * 8) + 2 * al(n * 8) + al(n * 8) + 6 * al(n * 4);
+    return al(tb) + 2 * al(n * 8) + 2 * al(n * 8) + al(n * 8) + 8 * al(n * 4);
 }
 
 // Builds a sorted copy of `L` in `ws`; fills `S` with device pointers into ws and
@@ -377,13 +385,15 @@ int sort_lines(const hk_lines *L, char *ws, hk_lines *S, int64_t **perm_out, cud
     auto *nu0 = (double *)take(n * 8);
     auto *S_ref = (float *)take(n * 4), *A = (float *)take(n * 4), *g_up = (float *)take(n * 4);
     auto *E = (float *)take(n * 4), *gam = (float *)take(n * 4), *nT = (float *)take(n * 4);
+    auto *gself = (float *)take(n * 4), *dlt = (float *)take(n * 4);
     int sms = num_sms();
     k_sort_keys<<<sms * 4, 256, 0, st>>>(L->nu0, n, k_in, i_in);
     cudaError_t e = cudaGetLastError();
     if (e) return fail_cuda(e);
     e = cub::DeviceRadixSort::SortPairs(temp, tb, k_in, k_out, i_in, i_out, n, 0, 64, st);
     if (e) return fail_cuda(e);
-    k_gather_fields<<<sms * 4, 256, 0, st>>>(*L, i_out, n, nu0, S_ref, A, g_up, E, gam, nT);
+    k_gather_fields<<<sms * 4, 256, 0, st>>>(*L, i_out, n, nu0, S_ref, A, g_up, E, gam, nT,
+                                             gself, dlt);
     if ((e = cudaGetLastError())) return fail_cuda(e);
     *S = *L;
     S->nu0 = nu0;
@@ -393,6 +403,8 @@ int sort_lines(const hk_lines *L, char *ws, hk_lines *S, int64_t **perm_out, cud
     S->E_low = E;
     S->gamma_ref = gam;
     S->n_T = nT;
+    S->gamma_self = L->gamma_self ? gself : nullptr;
+    S->delta = L->delta ? dlt : nullptr;
     S->sorted = 1;
     *perm_out = i_out;
     return HK_OK;
@@ -670,16 +682,16 @@ int hk_cross_section_host(const hk_lines *lines, const hk_grid *grid, const hk_s
     const int64_t C = std::max<int64_t>(1, std::min<int64_t>(chunk_lines > 0 ? chunk_lines
                                                                              : (int64_t)1 << 23,
                                                              std::max<int64_t>(n, 1)));
-    // float fields present (S_ref, E_low, gamma_ref, n_T, A, g_up)
-    const float *hf[6] = {lines->S_ref, lines->E_low, lines->gamma_ref, lines->n_T, lines->A,
-                          lines->g_up};
+    // float fields present (S_ref, E_low, gamma_ref, n_T, A, g_up, gamma_self, delta)
+    const float *hf[8] = {lines->S_ref, lines->E_low, lines->gamma_ref, lines->n_T, lines->A,
+                          lines->g_up,  lines->gamma_self, lines->delta};
     Tune t = get_tune(prec);
     const GridD g = make_grid(grid, opts);
     const size_t need_g = al(gather_workspace(1, nbins, prec, t.bpt));
     size_t cub_b = 0;
     const size_t sort_need = lines->sorted ? 0 : al(sort_bytes(C, &cub_b));
     size_t buf = al((size_t)C * 8);
-    for (int f = 0; f < 6; ++f)
+    for (int f = 0; f < 8; ++f)
         if (hf[f]) buf += al((size_t)C * 4);
     const size_t sig_b = al((size_t)nbins * 8);
     const size_t out_b = out_f64 ? sig_b : al((size_t)nbins * 4);
@@ -721,8 +733,9 @@ int hk_cross_section_host(const hk_lines *lines, const hk_grid *grid, const hk_s
                                  cx->cs)))
             return fail_cuda(e);
         cur += al((size_t)C * 8);
-        const float **lf[6] = {&L.S_ref, &L.E_low, &L.gamma_ref, &L.n_T, &L.A, &L.g_up};
-        for (int f = 0; f < 6; ++f) {
+        const float **lf[8] = {&L.S_ref, &L.E_low, &L.gamma_ref, &L.n_T,
+                               &L.A,     &L.g_up,  &L.gamma_self, &L.delta};
+        for (int f = 0; f < 8; ++f) {
             if (!hf[f]) continue;
             *lf[f] = (const float *)cur;
             if ((e = cudaMemcpyAsync(cur, hf[f] + off, sizeof(float) * cnt, cudaMemcpyDefault,
@@ -899,7 +912,8 @@ int hk_cross_section_backward(const hk_lines *lines, const hk_grid *grid, const 
     if (lines->n > 0 && (!dL_dSref || !dL_dgamma_ref)) return HK_EINVAL;
     if (lines->s_mode != HK_S_REF) return HK_ENOTSUP;
     if (opts->cut_mode == HK_CUT_DOPPLER || opts->cut_mode == HK_CUT_LORENTZ ||
-        (opts->flags & HK_REMOVE_PLINTH) || opts->profile != HK_PROFILE_VOIGT)
+        (opts->flags & HK_REMOVE_PLINTH) || opts->profile != HK_PROFILE_VOIGT ||
+        lines->gamma_self || lines->delta)
         return HK_ENOTSUP;
     for (int k = 0; k < nTP; ++k)
         if ((rc = check_state(&TP[k]))) return rc;

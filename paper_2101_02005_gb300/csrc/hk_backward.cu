@@ -201,7 +201,8 @@ __global__ void __launch_bounds__(BW_WARPS * 32, 4)
         const double nu0 = p0.nu0[l];
         int c, lo, hi;
         float rn;
-        const bool any = line_geometry_f32(nu0, g, line_cut(p0, g, l, nu0), &c, &rn, &lo, &hi);
+        const bool any =
+            line_geometry_f32(line_pos(p0, l), g, line_cut(p0, g, l, nu0), &c, &rn, &lo, &hi);
         double gS = 0.0, gG = 0.0;   // this lane's share of the line's gradients
         if (any) {
             const float nu0f = (float)nu0;

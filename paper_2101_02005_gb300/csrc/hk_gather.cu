@@ -82,7 +82,7 @@ __global__ void k_scale_prepass(const Prob *__restrict__ probs, int nprob, GridD
     int emax = INT_MIN;
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pr.n;
          l += (int64_t)gridDim.x * blockDim.x) {
-        const double nu0 = pr.nu0[l];
+        const double nu0 = line_pos(pr, l);
         if (!(nu0 > 0.0) || (g.W > 0.0 && (nu0 < nu_lo || nu0 > nu_hi))) continue;
         // approximate nearest-bin offset (float is enough for an exponent)
         float u = (float)(nu0 - g.nu_min) * (float)g.inv_dnu;
@@ -105,7 +105,7 @@ __global__ void k_scale_prepass(const Prob *__restrict__ probs, int nprob, GridD
     if ((threadIdx.x & 31) == 0 && emax != INT_MIN) atomicMax(pr.scale_exp, emax);
 }
 
-// ---- largest per-line cutting length (per-line cut modes) --------------------
+// ---- largest reach of a line: per-line cut plus pressure shift ----------------
 // Non-negative doubles order like their bit patterns, so an integer atomicMax
 // on the bits is a max on the values.
 __global__ void k_cut_max(const Prob *__restrict__ probs, int nprob, GridD g)
@@ -116,10 +116,13 @@ __global__ void k_cut_max(const Prob *__restrict__ probs, int nprob, GridD g)
     unsigned long long best = 0ull;
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pr.n;
          l += (int64_t)gridDim.x * blockDim.x) {
-        const double nu0 = pr.nu0[l];
-        if (!(nu0 > 0.0)) continue;
+        const double nu0 = pr.nu0[l], pos = line_pos(pr, l);
+        if (!(pos > 0.0)) continue;
         const CutW cw = line_cut(pr, g, l, nu0);
-        const double cut = __dmul_rn(cw.W, g.dnu) * (1.0 + 1e-12) + 1e-300;  // >= the cut
+        if (cw.nocut) continue;
+        // the reach of the line from its unshifted centre: cut plus |shift|
+        const double cut = __dmul_rn(cw.W, g.dnu) * (1.0 + 1e-12) + fabs(pos - nu0) * (1.0 + 1e-12) +
+                           1e-300;
         if (cut > 0.0 && cut < 1e300) best = max(best, (unsigned long long)__double_as_longlong(cut));
     }
     for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -157,7 +160,7 @@ __global__ void k_tile_ranges(const Prob *__restrict__ probs, int nprob, GridD g
     const Prob &pr = probs[p];
     int64_t lb = 0, le = pr.n;
     if (has_cut(g)) {
-        const double cut = g.W > 0.0 ? g.cut : *pr.cutmax;
+        const double cut = (g.W > 0.0 && !pr.delta) ? g.cut : *pr.cutmax;
         double lo_nu = g.nu_min + (double)(t * tile_bins) * g.dnu - cut - 2.0 * g.dnu;
         double hi_nu = g.nu_min + (double)(t * tile_bins + tile_bins - 1) * g.dnu + cut + 2.0 * g.dnu;
         lb = lower_bound_nu(pr.nu0, pr.n, lo_nu);
@@ -202,7 +205,7 @@ __device__ __forceinline__ void stage_line(const Prob &pr, const GridD &g, int64
     int i0, lo, hi;
     double r;
     const CutW cw = line_cut(pr, g, l, nu0);
-    bool any = line_geometry_w(nu0, g, cw.nocut, cw.W, &i0, &r, &lo, &hi);
+    bool any = line_geometry_w(line_pos(pr, l), g, cw.nocut, cw.W, &i0, &r, &lo, &hi);
     LineT<R> q;
     int c;
     double rn;
@@ -313,7 +316,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         const int scale = (sizeof(R) == 4) ? *pr.scale_exp : 0;
 
         const int wb0 = (int)(t * TILE) + warp * 32 * BPT;  // first bin of this warp
-        const double wcut = g.W > 0.0 ? g.cut : (has_cut(g) ? *pr.cutmax : 0.0);
+        const double wcut = (g.W > 0.0 && !pr.delta) ? g.cut : (has_cut(g) ? *pr.cutmax : 0.0);
         const double wnu_lo = g.nu_min + (double)wb0 * g.dnu - wcut - 2.0 * g.dnu;
         const double wnu_hi = g.nu_min + (double)(wb0 + 32 * BPT - 1) * g.dnu + wcut + 2.0 * g.dnu;
 
@@ -431,7 +434,8 @@ __global__ void k_count_pairs(Prob p, GridD g, unsigned long long *counts)
         int cb, lo, hi;
         float rnf;
         const double nu0 = p.nu0[l];
-        if (!line_geometry_f32(nu0, g, line_cut(p, g, l, nu0), &cb, &rnf, &lo, &hi)) continue;
+        if (!line_geometry_f32(line_pos(p, l), g, line_cut(p, g, l, nu0), &cb, &rnf, &lo, &hi))
+            continue;
         const double r = (double)rnf;
         double S, aDinv, y;
         line_strength_f64(p, l, &S, &aDinv, &y);
@@ -641,7 +645,9 @@ int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt,
         if ((e = cudaMemsetAsync(out, 0, sizeof(double) * (size_t)nprob * g.nbins, st)))
             return fail_cuda(e);
     }
-    if (g.cut_mode == kCutDoppler || g.cut_mode == kCutLorentz) {
+    bool shifted = false;
+    for (int p = 0; p < nprob; ++p) shifted |= probs_h[p].delta != nullptr;
+    if (g.cut_mode == kCutDoppler || g.cut_mode == kCutLorentz || (shifted && has_cut(g))) {
         if ((e = cudaMemsetAsync(cutmax, 0, sizeof(double) * nprob, st))) return fail_cuda(e);
         dim3 grid(num_sms * 4, nprob);
         k_cut_max<<<grid, 256, 0, st>>>(probs_d, nprob, g);

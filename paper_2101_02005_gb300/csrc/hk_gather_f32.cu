@@ -99,9 +99,8 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
     Rec q;
     int c, lo, hi;
     float rn;
-    const double nu0 = pr.nu0[l];
-    const CutW cw = line_cut(pr, g, l, nu0);
-    const bool any = line_geometry_f32(nu0, g, cw, &c, &rn, &lo, &hi);
+    const CutW cw = line_cut(pr, g, l, pr.nu0[l]);
+    const bool any = line_geometry_f32(line_pos(pr, l), g, cw, &c, &rn, &lo, &hi);
     q.c = c;
     q.lo = lo;
     q.hi = hi;

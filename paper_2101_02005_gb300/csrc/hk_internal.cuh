@@ -277,6 +277,10 @@ struct Prob {
     double inv_Pref;            // 1 / P_ref
     double nat_coef;            // 1 / (4 pi c)
     double tratio;              // T_ref / T
+    const float *gamma_self;    // HITRAN self widths (gamma is then gamma_air), or null
+    const float *delta;         // pressure shifts (cm^-1 per P_ref), or null
+    double press_air, press_self;   // (P - P_self) / P_ref, P_self / P_ref
+    float press_air_f, press_self_f;
     double K_D;                 // sqrt(ln 2) sqrt(2 k_B T / m) / c: Gamma_D = nu0 K_D
     const double *cutmax;       // device: largest cutting length of the lines (per-line modes)
     // the same scalars rounded to float (set with them on the host), for the
@@ -341,6 +345,14 @@ struct CutW {
     float Wf;
 };
 
+// Where line l sits on the grid: nu0, or nu0 + delta P / P_ref (FP64) with a
+// pressure shift.
+__device__ __forceinline__ double line_pos(const Prob &p, int64_t l)
+{
+    const double nu0 = p.nu0[l];
+    return p.delta ? __dadd_rn(nu0, __dmul_rn((double)p.delta[l], p.press)) : nu0;
+}
+
 __device__ __forceinline__ CutW line_cut(const Prob &p, const GridD &g, int64_t l, double nu0)
 {
     CutW c;
@@ -350,8 +362,12 @@ __device__ __forceinline__ CutW line_cut(const Prob &p, const GridD &g, int64_t 
             G = __dmul_rn(nu0, p.K_D);
         } else {
             const double nat = p.A ? __ddiv_rn((double)p.A[l], 4.0 * kPI * kC) : 0.0;
-            G = __dadd_rn(nat, __dmul_rn(__dmul_rn((double)p.gamma[l], pow(p.tratio, (double)p.n_T[l])),
-                                         p.press));
+            const double tn = pow(p.tratio, (double)p.n_T[l]);
+            G = p.gamma_self
+                    ? __dadd_rn(nat, __dmul_rn(tn, __dadd_rn(__dmul_rn((double)p.gamma[l], p.press_air),
+                                                             __dmul_rn((double)p.gamma_self[l],
+                                                                       p.press_self))))
+                    : __dadd_rn(nat, __dmul_rn(__dmul_rn((double)p.gamma[l], tn), p.press));
         }
         c.nocut = false;
         c.W = __dmul_rn(__dmul_rn(g.cut_factor, G), g.inv_dnu);
@@ -504,7 +520,10 @@ __device__ __forceinline__ void line_strength_f32(const Prob &p, int64_t l, floa
     const float nu0f = (float)p.nu0[l];
     float aDinv = p.aD_coef_f / nu0f;
     float nat = p.A ? p.A[l] * p.nat_coef_f : 0.0f;
-    float GL = nat + p.gamma[l] * exp2f(p.n_T[l] * p.log2_tratio_f) * p.press_f;
+    const float trn = exp2f(p.n_T[l] * p.log2_tratio_f);
+    float GL = p.gamma_self
+                   ? nat + trn * fmaf(p.gamma[l], p.press_air_f, p.gamma_self[l] * p.press_self_f)
+                   : nat + p.gamma[l] * trn * p.press_f;
     // log2 of the Boltzmann factor, E'' K2, as a float pair Lh + Ll: E'' is a
     // float, so E'' K2_hi has the exact error term fma(E'', K2_hi, -Lh)
     const float E = p.E_low[l];
@@ -534,7 +553,10 @@ __device__ __forceinline__ void line_strength_f64(const Prob &p, int64_t l, doub
     double nu0 = p.nu0[l];
     double aDinv = p.aD_coef / nu0;
     double nat = p.A ? (double)p.A[l] * p.nat_coef : 0.0;
-    double GL = nat + (double)p.gamma[l] * exp2((double)p.n_T[l] * p.log2_tratio) * p.press;
+    const double trn = exp2((double)p.n_T[l] * p.log2_tratio);
+    double GL = p.gamma_self ? nat + trn * ((double)p.gamma[l] * p.press_air +
+                                            (double)p.gamma_self[l] * p.press_self)
+                             : nat + (double)p.gamma[l] * trn * p.press;
     double bz = exp2((double)p.E_low[l] * p.K2);
     double S;
     if (p.s_mode == 0) {

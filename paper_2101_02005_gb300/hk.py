@@ -36,7 +36,8 @@ class hk_lines(ctypes.Structure):
     _fields_ = [("nu0", ctypes.c_void_p), ("S_ref", ctypes.c_void_p), ("A", ctypes.c_void_p),
                 ("g_up", ctypes.c_void_p), ("E_low", ctypes.c_void_p),
                 ("gamma_ref", ctypes.c_void_p), ("n_T", ctypes.c_void_p), ("n", ctypes.c_int64),
-                ("mass_amu", ctypes.c_double), ("s_mode", ctypes.c_int), ("sorted", ctypes.c_int)]
+                ("mass_amu", ctypes.c_double), ("s_mode", ctypes.c_int), ("sorted", ctypes.c_int),
+                ("gamma_self", ctypes.c_void_p), ("delta", ctypes.c_void_p)]
 
 
 class hk_grid(ctypes.Structure):
@@ -45,7 +46,7 @@ class hk_grid(ctypes.Structure):
 
 class hk_state(ctypes.Structure):
     _fields_ = [("T", ctypes.c_double), ("P", ctypes.c_double), ("Q_T", ctypes.c_double),
-                ("dlnQ_dT", ctypes.c_double)]
+                ("dlnQ_dT", ctypes.c_double), ("P_self", ctypes.c_double)]
 
 
 class hk_opts(ctypes.Structure):
@@ -137,17 +138,19 @@ class DeviceLines:
     g_up: Optional[torch.Tensor] = None
     s_mode: int = HK_S_REF
     sorted: bool = True
+    gamma_self: Optional[torch.Tensor] = None
+    delta: Optional[torch.Tensor] = None
 
     @property
     def n(self) -> int:
         return int(self.nu0.numel())
 
     def struct(self) -> hk_lines:
-        return hk_lines(self.nu0.data_ptr(), self.S_ref.data_ptr() if self.S_ref is not None else None,
-                        self.A.data_ptr() if self.A is not None else None,
-                        self.g_up.data_ptr() if self.g_up is not None else None,
+        p = lambda t: t.data_ptr() if t is not None else None
+        return hk_lines(self.nu0.data_ptr(), p(self.S_ref), p(self.A), p(self.g_up),
                         self.E_low.data_ptr(), self.gamma_ref.data_ptr(), self.n_T.data_ptr(),
-                        self.n, float(self.mass_amu), int(self.s_mode), int(bool(self.sorted)))
+                        self.n, float(self.mass_amu), int(self.s_mode), int(bool(self.sorted)),
+                        p(self.gamma_self), p(self.delta))
 
     @staticmethod
     def from_host(L, device="cuda", pin=False) -> "DeviceLines":
@@ -162,7 +165,9 @@ class DeviceLines:
         return DeviceLines(t(L.nu0, torch.float64), t(L.S_ref, torch.float32),
                            t(L.E_low, torch.float32), t(L.gamma_ref, torch.float32),
                            t(L.n_T, torch.float32), L.mass_amu, A=t(L.A, torch.float32),
-                           g_up=t(L.g_up, torch.float32), s_mode=L.s_mode, sorted=L.sorted)
+                           g_up=t(L.g_up, torch.float32), s_mode=L.s_mode, sorted=L.sorted,
+                           gamma_self=t(getattr(L, "gamma_self", None), torch.float32),
+                           delta=t(getattr(L, "delta", None), torch.float32))
 
 
 class HostLines(DeviceLines):
@@ -179,15 +184,17 @@ class HostLines(DeviceLines):
         return HostLines(t(L.nu0, torch.float64), t(L.S_ref, torch.float32),
                          t(L.E_low, torch.float32), t(L.gamma_ref, torch.float32),
                          t(L.n_T, torch.float32), L.mass_amu, A=t(L.A, torch.float32),
-                         g_up=t(L.g_up, torch.float32), s_mode=L.s_mode, sorted=L.sorted)
+                         g_up=t(L.g_up, torch.float32), s_mode=L.s_mode, sorted=L.sorted,
+                         gamma_self=t(getattr(L, "gamma_self", None), torch.float32),
+                         delta=t(getattr(L, "delta", None), torch.float32))
 
 
 def make_grid(nu_min, dnu, nbins) -> hk_grid:
     return hk_grid(float(nu_min), float(dnu), int(nbins))
 
 
-def make_state(T, P, Q_T, dlnQ_dT=0.0) -> hk_state:
-    return hk_state(float(T), float(P), float(Q_T), float(dlnQ_dT))
+def make_state(T, P, Q_T, dlnQ_dT=0.0, P_self=0.0) -> hk_state:
+    return hk_state(float(T), float(P), float(Q_T), float(dlnQ_dT), float(P_self))
 
 
 def make_opts(Q_Tref, cut, precision=HK_FP32C, T_ref=296.0, P_ref=1.0, cut_mode=None,

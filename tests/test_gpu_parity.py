@@ -239,6 +239,37 @@ def test_line_profiles(hk, prec):
         assert d[m].sum() <= 1e-5 * base[m].sum(), what
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_hitran_widths_and_pressure_shift(hk, prec):
+    """HITRAN air/self widths (Eq. gammaL) and pressure-shifted positions on a
+    config-0-shaped list: device-resident (sorted and unsorted) and streamed
+    from host memory, against the oracle; pair totals on the shifted
+    positions equal the oracle's."""
+    L = synth.make_lines(3000, 0.0, 3000.0, synth.SEED_BASE + 7, 18.0, hitran=True)
+    grid = synth.Grid(0.0, 0.1, 30000)
+    T, P, Ps, cut = 900.0, 3.0, 0.8, 25.0
+    ref = oracle.cross_section(L.as_oracle(), grid.astuple(), (T, P, float(Q(T)), QREF), cut,
+                               P_self=Ps)
+    st = hk.make_state(T, P, float(Q(T)), P_self=Ps)
+    g = hk.make_grid(*grid.astuple())
+    opts = hk.make_opts(QREF, cut, prec, flags=hk.HK_SIGMA_F64)
+    D = hk.DeviceLines.from_host(L)
+    pos = oracle.shift(L.nu0, L.delta, P)
+    assert hk.hk_count_pairs(D, g, st, opts)[0] == oracle.count_pairs(pos, *grid.astuple(), cut)
+    got = hk.hk_cross_section(D, g, st, opts)
+    hk.hk_sync_status()
+    assert_sigma_close(got.cpu().numpy(), ref, f"hitran prec={prec}")
+    perm = np.random.default_rng(9).permutation(L.n)
+    U = L.subset(perm)
+    U.sorted = False
+    got = hk.hk_cross_section(hk.DeviceLines.from_host(U), g, st, opts)
+    hk.hk_sync_status()
+    assert_sigma_close(got.cpu().numpy(), ref, f"hitran unsorted prec={prec}")
+    got = hk.hk_cross_section_host(hk.HostLines.from_host(L), g, st, opts, chunk_lines=700)
+    hk.hk_sync_status()
+    assert_sigma_close(got.numpy(), ref, f"hitran host prec={prec}")
+
+
 def test_backward_rejects_plinth_and_per_line_cuts(hk):
     L = synth.make_lines(50, 0.0, 10.0, 3, 18.0)
     D = hk.DeviceLines.from_host(L)
@@ -251,6 +282,10 @@ def test_backward_rejects_plinth_and_per_line_cuts(hk):
         with pytest.raises(hk.HKError) as e:
             hk.hk_cross_section_backward(D, grid, st, opts, g)
         assert e.value.status == hk.HK_ENOTSUP
+    H = hk.DeviceLines.from_host(synth.make_lines(50, 0.0, 10.0, 3, 18.0, hitran=True))
+    with pytest.raises(hk.HKError) as e:
+        hk.hk_cross_section_backward(H, grid, st, hk.make_opts(QREF, 2.0), g)
+    assert e.value.status == hk.HK_ENOTSUP
 
 
 def test_zero_lines_and_single_line(hk):
