@@ -316,9 +316,15 @@ int hk_workspace_size(int kind, const hk_lines *species, int nspecies, int nTP,
 int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
                 const hk_opts *opts, void *stream);
 
-/* The lines-per-item setting in use for a precision (the default 16384 until
+/* The lines-per-item setting in use for a precision (defaults 2048 for
+ * HK_FP32C and 16384 for HK_FP64 until
  * hk_autotune has run on this device).  lmax: HOST int. */
 int hk_tuning(int precision, int *lmax);
+
+/* Sets the lines-per-item setting for a precision on the current device, e.g.
+ * to reuse a value hk_autotune found in an earlier process (no paper
+ * counterpart).  lmax: 32 .. 2^24, else HK_EINVAL. */
+int hk_set_tuning(int precision, int lmax);
 
 /* Instrumentation (no counterpart in the paper).  Counts the (line, bin)
  * pairs the cut admits for this problem: counts[0] = total (the algorithmic

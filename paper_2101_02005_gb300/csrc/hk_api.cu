@@ -134,6 +134,7 @@ static Tune get_tune(int precision)
     if (it != g_tune.end()) return it->second;
     Tune t;
     if (precision == HK_FP64) t.bpt = 2;
+    else t.lmax = 2048;   // what hk_autotune picks for the benchmark's line lists
     return t;
 }
 
@@ -957,7 +958,8 @@ int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *stat
     // lines per work item: small items balance uneven line density across the
     // SMs, large ones cut the per-item cost (record setup, one FP64 atomic per
     // bin of the tile)
-    const int lmaxs[] = {2048, 8192, 32768, 131072};
+    const int lmaxs[] = {1024, 2048, 4096, 16384, 65536};
+    const int ncand = (int)(sizeof(lmaxs) / sizeof(lmaxs[0]));
     size_t out_b = (size_t)grid->nbins * 8;
     // the output buffer lives in its own cudaMalloc (the pool is used by the runs)
     void *out = nullptr;
@@ -972,7 +974,7 @@ int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *stat
     o.flags |= HK_SIGMA_F64;  // time without any float-overflow concern
     Tune best = get_tune(prec);
     float best_ms = 1e30f;
-    for (int j = 0; j < 4 && rc == HK_OK; ++j) {
+    for (int j = 0; j < ncand && rc == HK_OK; ++j) {
         rc = cross_section_impl(lines, grid, state, &o, out, st, bpt, lmaxs[j]);  // warm-up
         if (rc) break;
         cudaEventRecord(e0, st);
@@ -1007,6 +1009,20 @@ int hk_tuning(int precision, int *lmax)
 {
     if ((precision != HK_FP32C && precision != HK_FP64) || !lmax) return HK_EINVAL;
     *lmax = get_tune(precision).lmax;
+    return HK_OK;
+}
+
+int hk_set_tuning(int precision, int lmax)
+{
+    if ((precision != HK_FP32C && precision != HK_FP64) || lmax < 32 || lmax > (1 << 24))
+        return HK_EINVAL;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return fail_cuda(e);
+    Tune t = get_tune(precision);
+    t.lmax = lmax;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[{dev, precision}] = t;
     return HK_OK;
 }
 

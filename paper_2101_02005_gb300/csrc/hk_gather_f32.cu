@@ -35,7 +35,7 @@ constexpr int NW = 8;             // warps per block
 constexpr int NT = NW * 32;
 constexpr int TILE = 1024;        // bins per tile
 constexpr int QCAP = 64;          // core-queue entries per warp
-constexpr int FLUSH_ROUNDS = 2;   // rounds (32 lines per warp each) between two-sum folds
+constexpr int FLUSH_ROUNDS = 4;   // rounds (32 lines per warp each) between two-sum folds
 
 // Per-line record, computed once per (line, item) by one lane.  Groups are
 // aligned to absolute bin indices: group g holds bins [32 g, 32 g + 31], so a

@@ -29,7 +29,7 @@ EXPORTS = ["hk_line_strength", "hk_widths", "hk_voigt_accumulate", "hk_cross_sec
            "hk_cross_section_batched", "hk_cross_section_backward", "hk_workspace_size",
            "hk_autotune", "hk_sync_status", "hk_release", "hk_strerror", "hk_last_cuda_error",
            "hk_constants", "hk_version", "hk_count_pairs", "hk_profile",
-           "hk_cross_section_noalloc", "hk_tuning", "hk_cross_section_host"]
+           "hk_cross_section_noalloc", "hk_tuning", "hk_cross_section_host", "hk_set_tuning"]
 
 
 class hk_lines(ctypes.Structure):
@@ -100,6 +100,7 @@ def lib():
                                  P(ctypes.c_int64), vp]
     L.hk_profile.argtypes = [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int64)]
     L.hk_tuning.argtypes = [ctypes.c_int, P(ctypes.c_int)]
+    L.hk_set_tuning.argtypes = [ctypes.c_int, ctypes.c_int]
     L.hk_cross_section_noalloc.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts),
                                            vp, vp]
     L.hk_cross_section_host.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts), vp,
@@ -365,6 +366,11 @@ def hk_tuning(precision: int = HK_FP32C) -> int:
     v = ctypes.c_int(0)
     _check("hk_tuning", lib().hk_tuning(int(precision), ctypes.byref(v)))
     return int(v.value)
+
+
+def hk_set_tuning(precision: int, lmax: int):
+    """Sets the lines-per-item setting of `precision` on the current device."""
+    _check("hk_set_tuning", lib().hk_set_tuning(int(precision), int(lmax)))
 
 
 def hk_sync_status(stream=None):
