@@ -165,6 +165,23 @@ def cpu_sample(w, L, T, P, seconds_target=15.0, nthreads=0):
     return pairs / max(t_used, 1e-9), t_used, pairs, wins
 
 
+def max_over_ranks(ms_local, dist, device):
+    """The slowest rank's elapsed time (ms): every rank's timed region is
+    bracketed by a barrier, and the job takes as long as its slowest rank."""
+    if dist is None:
+        return float(ms_local)
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms_max, steps):
+    """Whole-job throughput: the units all ranks processed per second (weak
+    scaling: every rank processes units_per_rank per step)."""
+    return world * units_per_rank / (ms_max / steps / 1e3)
+
+
 def w_seed_offset(w):
     return 1 if w.name.startswith("c1") else (2 if w.name.startswith("c2") else 0)
 
@@ -285,13 +302,9 @@ def main():
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     hk.hk_sync_status()
-    ms_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist, dev)
     ms_step = ms_max / args.steps
-    value = world * L.n / (ms_step / 1e3)
+    value = job_rate(L.n, world, ms_max, args.steps)
 
     # roofline of the dominant kernel (the Voigt gather), live CUDA-event time
     peaks = load_peaks()
@@ -335,12 +348,8 @@ def main():
             e2e_step()
         f1.record(stream)
         barrier()
-        ems = f0.elapsed_time(f1)
-        if dist is not None:
-            t = torch.tensor([ems], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * L.n / (ems / args.steps / 1e3), "unit": "lines/s",
+        ems = max_over_ranks(f0.elapsed_time(f1), dist, dev)
+        e2e = {"value": job_rate(L.n, world, ems, args.steps), "unit": "lines/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": ems / args.steps, "call": "hk_cross_section_host",
                "block_lines": 1 << 23}
