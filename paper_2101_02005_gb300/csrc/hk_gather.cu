@@ -72,34 +72,52 @@ __device__ __forceinline__ int sampled_peak_exp2(float x_n, float y, int profile
     return B > 0.0f && B < INFINITY ? ilogbf(B) : INT_MIN / 2;
 }
 
+// One line's largest sampled value as a power-of-two exponent (INT_MIN if it
+// adds nothing).
+// Only an exponent is needed, so the position, the coarse grid-range test and
+// the nearest-bin offset are float (FP64 runs at a small fraction of the FP32
+// rate and would dominate this pass): a line at the edge of the range may be
+// counted or skipped, which moves the scale, never the sum.
+__device__ __forceinline__ int line_peak_exp(const Prob &pr, const GridD &g, int64_t l,
+                                             float nu_lo, float nu_hi, float nu_min,
+                                             float inv_dnu)
+{
+    const float nu0 = (float)(pr.delta ? line_pos(pr, l) : pr.nu0[l]);
+    if (!(nu0 > 0.0f) || (g.W > 0.0 && (nu0 < nu_lo || nu0 > nu_hi))) return INT_MIN;
+    float u = (nu0 - nu_min) * inv_dnu;
+    float rn = fabsf(u - rintf(u));
+    if (pr.pre) {
+        double v = pr.S_pre[l] * (double)pr.aDinv_pre[l] * kInvSqrtPi;
+        float b = (float)g.dnu * pr.aDinv_pre[l];
+        return v > 0.0 ? ilogb(v) + sampled_peak_exp2(rn * b, pr.y_pre[l], kProfVoigt, b)
+                       : INT_MIN;
+    }
+    float P, aDinv, y;
+    int e2;
+    line_strength_f32(pr, l, &P, &e2, &aDinv, &y);
+    float b = (float)g.dnu * aDinv;
+    return P > 0.0f ? ilogbf(P) + e2 + sampled_peak_exp2(rn * b, y, g.profile, b) : INT_MIN;
+}
+
+// Four lines per thread and iteration, so that each thread has the loads of
+// four lines in flight (the pass is a stream over the line list).
 __global__ void k_scale_prepass(const Prob *__restrict__ probs, int nprob, GridD g)
 {
     int p = blockIdx.y;
     if (p >= nprob) return;
     const Prob &pr = probs[p];
-    const double nu_lo = g.nu_min - g.cut - g.dnu;
-    const double nu_hi = g.nu_min + (double)g.nbins * g.dnu + g.cut + g.dnu;
+    const float nu_lo = (float)(g.nu_min - g.cut - 2.0 * g.dnu);
+    const float nu_hi = (float)(g.nu_min + (double)g.nbins * g.dnu + g.cut + 2.0 * g.dnu);
+    const float nu_min = (float)g.nu_min, inv_dnu = (float)g.inv_dnu;
     int emax = INT_MIN;
-    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pr.n;
-         l += (int64_t)gridDim.x * blockDim.x) {
-        const double nu0 = line_pos(pr, l);
-        if (!(nu0 > 0.0) || (g.W > 0.0 && (nu0 < nu_lo || nu0 > nu_hi))) continue;
-        // approximate nearest-bin offset (float is enough for an exponent)
-        float u = (float)(nu0 - g.nu_min) * (float)g.inv_dnu;
-        float rn = fabsf(u - rintf(u));
-        int e;
-        if (pr.pre) {
-            double v = pr.S_pre[l] * (double)pr.aDinv_pre[l] * kInvSqrtPi;
-            float b = (float)g.dnu * pr.aDinv_pre[l];
-            e = v > 0.0 ? ilogb(v) + sampled_peak_exp2(rn * b, pr.y_pre[l], kProfVoigt, b) : INT_MIN;
-        } else {
-            float P, aDinv, y;
-            int e2;
-            line_strength_f32(pr, l, &P, &e2, &aDinv, &y);
-            float b = (float)g.dnu * aDinv;
-            e = P > 0.0f ? ilogbf(P) + e2 + sampled_peak_exp2(rn * b, y, g.profile, b) : INT_MIN;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < pr.n; l += 4 * stride) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t lk = l + k * stride;
+            if (lk < pr.n)
+                emax = max(emax, line_peak_exp(pr, g, lk, nu_lo, nu_hi, nu_min, inv_dnu));
         }
-        emax = max(emax, e);
     }
     for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
     if ((threadIdx.x & 31) == 0 && emax != INT_MIN) atomicMax(pr.scale_exp, emax);
