@@ -231,11 +231,28 @@ __global__ void __launch_bounds__(BW_WARPS * 32, 4)
                     const float *gk = grad + (int64_t)(kc + j) * g.nbins;
                     float sV = 0.0f, sXVx = 0.0f, sVy = 0.0f;
                     float kf = k0 + (float)lane;
-                    for (int i = lo + lane; i <= hi; i += 32, kf += 32.0f) {
+                    int i = lo + lane;
+                    // four bins per lane and step, their upstream-gradient loads
+                    // issued before any profile work (the loop is load-latency bound)
+                    for (; i + 96 <= hi; i += 128, kf += 128.0f) {
+                        float gv[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) gv[u] = __ldg(gk + i + 32 * u);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const float x = fmaf(kf + 32.0f * u, bstep, -rnb);
+                            float V, Vx, Vy;
+                            voigt_grad(x, y, &V, &Vx, &Vy);
+                            sV = fmaf(gv[u], V, sV);
+                            sXVx = fmaf(gv[u] * x, Vx, sXVx);
+                            sVy = fmaf(gv[u], Vy, sVy);
+                        }
+                    }
+                    for (; i <= hi; i += 32, kf += 32.0f) {
+                        const float gi = __ldg(gk + i);
                         const float x = fmaf(kf, bstep, -rnb);
                         float V, Vx, Vy;
                         voigt_grad(x, y, &V, &Vx, &Vy);
-                        const float gi = __ldg(gk + i);
                         sV = fmaf(gi, V, sV);
                         sXVx = fmaf(gi * x, Vx, sXVx);
                         sVy = fmaf(gi, Vy, sVy);
