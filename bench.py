@@ -341,6 +341,9 @@ def main():
 
         e2e_step()
         barrier()
+        esampler = ClockSampler(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+        esampler.start()
+        time.sleep(0.3)
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -348,11 +351,12 @@ def main():
             e2e_step()
         f1.record(stream)
         barrier()
+        eclocks = esampler.stop()
         ems = max_over_ranks(f0.elapsed_time(f1), dist, dev)
         e2e = {"value": job_rate(L.n, world, ems, args.steps), "unit": "lines/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": ems / args.steps, "call": "hk_cross_section_host",
-               "block_lines": 1 << 23}
+               "block_lines": 1 << 23, "clocks": eclocks}
         del H
 
     # the plain FP64 GPU form on every 10th line (per-line work is the same
