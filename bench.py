@@ -37,9 +37,9 @@ METRIC = "lines/s and Voigt evals/s on 1 GB300 (FP32-comp vs FP64 GPU) at stated
 # are four-node work here.
 FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 25, "gh4": 25, "core": 200}
 # DRAM bytes per line of one k_gather_f32 launch, from the ncu capture in
-# profiles/k_gather_f32_config1-1e7-lines.md (277.9 MB for 1e7 lines; traffic
+# profiles/k_gather_f32_config1-1e7-lines.md (245.9 MB for 1e7 lines; traffic
 # grows with the line count).  Set to None when the kernel changes.
-GATHER_DRAM_BYTES_PER_LINE = 27.79
+GATHER_DRAM_BYTES_PER_LINE = 24.59
 FP32_LANES_PER_SM = 128
 
 
@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time hk_cross_section_backward over all (T, P) points of the "
+                         "workload (config 4) instead of the forward step")
     return ap.parse_args()
 
 
@@ -224,6 +227,40 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args, w, hk, synth, dev):
+    """The adjoint of the workload's (T, P) points (config 4: dL/dT, dL/dP and
+    per-line dL/dS_ref, dL/dgamma_ref from an N(0, 1) upstream gradient)."""
+    import torch
+    Q = synth.partition_function
+    L = w.species[0]
+    pts = w.states()
+    D = hk.DeviceLines.from_host(L)
+    grid = hk.make_grid(*w.grid.astuple())
+    opts = hk.make_opts(float(Q(296.0)), w.cut)
+    states = [hk.make_state(t, p, float(Q(t)), float(synth.dlnQ_dT(t))) for t, p in pts]
+    g = torch.from_numpy(synth.upstream_grad(len(pts), w.grid.nbins,
+                                             synth.SEED_BASE + args.config)).to(dev)
+    pairs = sum(hk.hk_count_pairs(D, grid, s, opts)[0] for s in states)
+    for _ in range(args.warmup):
+        hk.hk_cross_section_backward(D, grid, states, opts, g)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        hk.hk_cross_section_backward(D, grid, states, opts, g)
+    e1.record()
+    torch.cuda.synchronize()
+    hk.hk_sync_status()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"metric": "adjoint line-points/s", "value": L.n * len(pts) / (ms / 1e3),
+                      "unit": "line-points/s", "ms_per_step": ms, "steps": args.steps,
+                      "warmup": args.warmup, "derivative_evals_per_s": pairs / (ms / 1e3),
+                      "higher_is_better": True,
+                      "config": {"workload": w.name, "lines": L.n, "points": len(pts),
+                                 "pairs_per_step": pairs}}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -253,6 +290,9 @@ def main():
     T, P = w.states()[0]
     Q = synth.partition_function
     t_gen = time.perf_counter() - t_gen
+    if args.adjoint:
+        run_adjoint(args, w, hk, synth, dev)
+        return
 
     # line list resident in HBM; pinned host copies for the end-to-end timing
     host = {k: torch.from_numpy(getattr(L, k)) for k in ("nu0", "S_ref", "E_low", "gamma_ref", "n_T")}
