@@ -270,6 +270,41 @@ def test_hitran_widths_and_pressure_shift(hk, prec):
     assert_sigma_close(got.numpy(), ref, f"hitran host prec={prec}")
 
 
+def test_batched_with_profiles_plinth_and_per_line_cuts(hk):
+    """The batched launch with a non-Voigt profile, the plinth and a per-line
+    cut: every (species, T, P) array equals the single-problem call on the
+    same options (same kernels, one launch), and one array against the
+    oracle."""
+    w = synth.config(3, scale=1e-4)
+    grid = synth.Grid(0.0, 0.01, 100000)
+    species = [hk.DeviceLines.from_host(s_) for s_ in w.species]
+    pts = [(float(t), float(p)) for t in w.T[::10] for p in w.P[::5]]
+    states = [hk.make_state(t, p, float(Q(t))) for t, p in pts]
+    g = hk.make_grid(*grid.astuple())
+    for prof, mode, cut in [(hk.HK_PROFILE_DOPPLER, hk.HK_CUT_DOPPLER, 400.0),
+                            (hk.HK_PROFILE_VOIGT, hk.HK_CUT_LORENTZ, 300.0)]:
+        opts = hk.make_opts(QREF, cut, cut_mode=mode, profile=prof,
+                            flags=hk.HK_SIGMA_F64 | hk.HK_REMOVE_PLINTH)
+        out = hk.hk_cross_section_batched(species, states, g, opts)
+        hk.hk_sync_status()
+        out = out.cpu().numpy()
+        for si, D in enumerate(species):
+            for k, st in enumerate(states):
+                one = hk.hk_cross_section(D, g, st, opts)
+                hk.hk_sync_status()
+                e = sigma_errors(out[si, k], one.cpu().numpy())
+                assert e["max_bin"] <= 1e-6, (prof, si, k, e)
+        t, p = pts[-1]
+        L = w.species[-1]
+        ref = oracle.cross_section(L.as_oracle(), grid.astuple(), (t, p, float(Q(t)), QREF), cut,
+                                   cut_mode=mode, plinth=True, profile=prof)
+        base = oracle.cross_section(L.as_oracle(), grid.astuple(), (t, p, float(Q(t)), QREF), cut,
+                                    cut_mode=mode, plinth=False, profile=prof)
+        m = base > 1e-10 * base.max()
+        d = np.abs(out[-1, -1] - ref)
+        assert np.max(d[m] / base[m]) <= 1e-4 and d[m].sum() <= 1e-5 * base[m].sum(), prof
+
+
 def test_backward_rejects_plinth_and_per_line_cuts(hk):
     L = synth.make_lines(50, 0.0, 10.0, 3, 18.0)
     D = hk.DeviceLines.from_host(L)
