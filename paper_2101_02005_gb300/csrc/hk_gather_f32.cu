@@ -5,15 +5,20 @@
 // * Work items are (problem, tile of TILE bins, chunk of <= lmax lines), as
 //   in the FP64 gather; a persistent grid pulls them from an atomic counter.
 // * Inside an item every warp takes 32 lines at a time: lane i computes the
-//   parameters of line i once (bin geometry in FP64, strength and widths in
-//   FP32, band boundaries) into a per-warp record table; then the warp sweeps
-//   each line's bins inside the tile, 32 consecutive bins per step (lane =
-//   bin); only the line's first and last groups are masked against the cut.
+//   parameters of line i once (the centre-to-bin offset in FP64, the cut
+//   bounds from FP32 sums away from ties, strength and widths in FP32, band
+//   boundaries, the plinth) into a per-warp record table; then the warp
+//   sweeps each line's bins inside the tile, 32 consecutive bins per step
+//   (lane = bin).  Only a line's first and last groups can be partial: the
+//   masked instance tests every group (short lines), the peeled one only
+//   those two (wide lines).
 // * The Faddeeva band of a 32-bin group is the band of its bin nearest the
 //   line centre.  The bands form nested intervals of group indices around
 //   the centre, computed once per line, so each group runs one formula with
 //   no divergence.  Bins of the central groups that fall in the core band
-//   (r2 < 64) go to a per-warp queue and are evaluated 32 at a time.
+//   (r2 < 64) go to a per-warp queue and are evaluated 32 at a time.  The
+//   Lorentzian profile is the one-node band on every group; the Doppler and
+//   binned-Gaussian profiles run one formula per line in their own instances.
 // * Each warp adds into its own FP32 copy of the tile in shared memory
 //   (consecutive bins, no bank conflicts, no atomics); every FLUSH_ROUNDS
 //   rounds the copies are summed into a (hi, lo) two-sum pair per bin, and at
