@@ -335,10 +335,8 @@ __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1
     }
     sweep<kBandGH1, V>(q, q.gA, q.L2 - 1, ga, gb, tg0, base, kfc, lane);
     sweep<kBandGH2, V>(q, q.L2, q.L4 - 1, ga, gb, tg0, base, kfc, lane);
-    sweep<kBandGH4, V>(q, q.L4, q.Lc - 1, ga, gb, tg0, base, kfc, lane);
-    if (q.Lc <= q.Rc)
-        sweep_core<V>(q, slot, q.Lc, q.Rc, ga, gb, tg0, base, kfc, lane, queue, qn, S, warp, t0);
-    sweep<kBandGH4, V>(q, q.Rc + 1, q.R4, ga, gb, tg0, base, kfc, lane);
+    if (q.L4 <= q.R4)   // the four-node groups and the core groups in one pass
+        sweep_core<V>(q, slot, q.L4, q.R4, ga, gb, tg0, base, kfc, lane, queue, qn, S, warp, t0);
     sweep<kBandGH2, V>(q, q.R4 + 1, q.R2, ga, gb, tg0, base, kfc, lane);
     sweep<kBandGH1, V>(q, q.R2 + 1, q.gB, ga, gb, tg0, base, kfc, lane);
 }
