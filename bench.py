@@ -34,7 +34,9 @@ METRIC = "lines/s and Voigt evals/s on 1 GB300 (FP32-comp vs FP64 GPU) at stated
 # node, r2 >= 1.5e6), 8 (two nodes, r2 >= 2500), 19 (four nodes, r2 >= 64)
 # and ~194 for the trapezoid core (r2 < 64).  hk_count_pairs splits the
 # four-node range at r2 = 200 (the FP64 kernel's three-node band): both parts
-# are four-node work here.
+# are four-node work here.  For short lines the kernel evaluates the one-node
+# region with the two-node rule (fewer passes per line); the model still counts
+# the one-node rule's 8 flops there, so it under-reports rather than inflates.
 FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 25, "gh4": 25, "core": 200}
 # DRAM bytes per line of one k_gather_f32 launch, from the ncu capture in
 # profiles/k_gather_f32_config1-1e7-lines.md (245.9 MB for 1e7 lines; traffic

@@ -333,12 +333,22 @@ __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1
         sweep<kBandBinned, V>(q, q.gA, q.gB, ga, gb, tg0, base, kfc, lane);
         return;
     }
-    sweep<kBandGH1, V>(q, q.gA, q.L2 - 1, ga, gb, tg0, base, kfc, lane);
-    sweep<kBandGH2, V>(q, q.L2, q.L4 - 1, ga, gb, tg0, base, kfc, lane);
+    // short lines (no kVPeel): the one-node region takes the two-node rule, one
+    // pass fewer on each side for a few more flops per far-wing pair
+    if (V & kVPeel) {
+        sweep<kBandGH1, V>(q, q.gA, q.L2 - 1, ga, gb, tg0, base, kfc, lane);
+        sweep<kBandGH2, V>(q, q.L2, q.L4 - 1, ga, gb, tg0, base, kfc, lane);
+    } else {
+        sweep<kBandGH2, V>(q, q.gA, q.L4 - 1, ga, gb, tg0, base, kfc, lane);
+    }
     if (q.L4 <= q.R4)   // the four-node groups and the core groups in one pass
         sweep_core<V>(q, slot, q.L4, q.R4, ga, gb, tg0, base, kfc, lane, queue, qn, S, warp, t0);
-    sweep<kBandGH2, V>(q, q.R4 + 1, q.R2, ga, gb, tg0, base, kfc, lane);
-    sweep<kBandGH1, V>(q, q.R2 + 1, q.gB, ga, gb, tg0, base, kfc, lane);
+    if (V & kVPeel) {
+        sweep<kBandGH2, V>(q, q.R4 + 1, q.R2, ga, gb, tg0, base, kfc, lane);
+        sweep<kBandGH1, V>(q, q.R2 + 1, q.gB, ga, gb, tg0, base, kfc, lane);
+    } else {
+        sweep<kBandGH2, V>(q, q.R4 + 1, q.gB, ga, gb, tg0, base, kfc, lane);
+    }
 }
 
 __device__ __forceinline__ void fold(Smem &S, int tid)
@@ -484,7 +494,10 @@ int gather_f32_launch(const Prob *probs_d, const GridD &g, int64_t ntiles, int64
                       int lmax, unsigned long long *counter, cudaStream_t st, int num_sms)
 {
     const bool wide = g.W <= 0.0 || 2.0 * g.W + 1.0 >= kPeelBins;
-    int v = (wide ? f32g::kVPeel : 0) | (g.plinth && has_cut(g) ? f32g::kVPlinth : 0);
+    // the Lorentzian is the one-node rule itself: it needs the one-node passes
+    // that only the peeled instance keeps
+    int v = (wide || g.profile == kProfLorentz ? f32g::kVPeel : 0) |
+            (g.plinth && has_cut(g) ? f32g::kVPlinth : 0);
     if (g.profile == kProfDoppler) v = f32g::kVPeel | f32g::kVPlinth | f32g::kVDoppler;
     if (g.profile == kProfBinned) v = f32g::kVPeel | f32g::kVPlinth | f32g::kVBinned;
     switch (v) {
