@@ -49,7 +49,18 @@
  *     fused multiply-add), bin i is inside iff |(i - i0) - r| <= W; cut <= 0
  *     means no cut (the whole grid).  Mathematically this is
  *     |nu_i - nu0| <= cut; the FP64 form fixes the decision at ties;
- *   - a line with nu0 <= 0 has no Doppler width (Eq. gammaD) and adds nothing.
+ *   - a line with nu0 <= 0 has no Doppler width (Eq. gammaD) and adds nothing;
+ *   - plinth (Sect. 2.1): the line's own profile value at exactly its cutting
+ *     length, subtracted from every bin inside the cut; no cut, no plinth;
+ *   - per-line cuts (Sect. 2.4.3 item 4): factor times the Doppler half width
+ *     sqrt(ln 2) alpha_D, evaluated as factor * (nu0 * K_D), or factor times
+ *     Gamma_L;
+ *   - profiles (Sect. 2.1): Lorentzian (Gamma_L/pi)/(d^2 + Gamma_L^2), Doppler
+ *     exp(-(d/alpha_D)^2)/(alpha_D sqrt(pi)), and the binned Gaussian as the
+ *     Doppler profile averaged over the bin [d - dnu/2, d + dnu/2];
+ *   - HITRAN lists (Sect. 2.2, Eq. gammaL): air/self widths with the self
+ *     partial pressure; the pressure shift moves the line to nu0 + delta P/P_ref
+ *     while S(T) and alpha_D keep nu0.
  */
 #include <complex.h>
 #include <math.h>
