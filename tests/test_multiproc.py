@@ -1,9 +1,9 @@
 """The N > 1 host logic of bench.py on CPU: two processes over gloo.
 
-Every GPU machine here holds one GPU, so multi-GPU runs are replicas (weak
-scaling, no data-path collective): the only cross-rank operations are the
-barrier and the max-reduce of the timed region, checked here with gloo, and
-the reference arm, which rank 0 alone runs under torchrun.
+Multi-GPU runs of the benchmark are independent replicas (weak scaling, no
+data-path collective): the only cross-rank operations are the barrier and the
+max-reduce of the timed region, checked here with gloo, and the reference arm,
+which rank 0 alone runs under torchrun.
 """
 import json
 import os
