@@ -76,3 +76,29 @@ def test_invalid_arguments_rejected_on_host(hk):
     out = ctypes.c_size_t(0)
     assert L.hk_workspace_size(2, b(lines), 1, 1, b(grid), b(op), b(out)) == hk.HK_EINVAL
     assert L.hk_constants(None) == hk.HK_EINVAL
+
+
+def test_new_options_validated_on_host(hk):
+    """Cut modes, profiles, flags, the self pressure and the tuning setter are
+    checked before any device work."""
+    L = hk.lib()
+    lines = hk.hk_lines(1, 2, None, None, 3, 4, 5, 10, 18.0, 0, 1)
+    grid = hk.make_grid(0.0, 0.1, 100)
+    st = hk.make_state(1000.0, 1.0, 3000.0)
+    b = ctypes.byref
+    for bop in (hk.make_opts(500.0, 0.0, cut_mode=hk.HK_CUT_DOPPLER),       # factor must be > 0
+                hk.make_opts(500.0, -3.0, cut_mode=hk.HK_CUT_LORENTZ),
+                hk.make_opts(500.0, 25.0, cut_mode=9),
+                hk.make_opts(500.0, 25.0, profile=4),
+                hk.make_opts(500.0, 25.0, profile=-1),
+                hk.make_opts(500.0, 25.0, flags=8)):
+        assert L.hk_cross_section(b(lines), b(grid), b(st), b(bop), 1, None) == hk.HK_EINVAL
+        assert L.hk_cross_section_host(b(lines), b(grid), b(st), b(bop), 1, 0, None) == hk.HK_EINVAL
+    op = hk.make_opts(500.0, 25.0)
+    bst = hk.make_state(1000.0, 1.0, 3000.0, P_self=-0.1)
+    assert L.hk_cross_section(b(lines), b(grid), b(bst), b(op), 1, None) == hk.HK_EINVAL
+    assert L.hk_cross_section_host(b(lines), b(grid), b(st), b(op), 1, -5, None) == hk.HK_EINVAL
+    assert L.hk_set_tuning(hk.HK_FP32C, 8) == hk.HK_EINVAL
+    assert L.hk_set_tuning(7, 2048) == hk.HK_EINVAL
+    v = ctypes.c_int(0)
+    assert L.hk_tuning(7, b(v)) == hk.HK_EINVAL
