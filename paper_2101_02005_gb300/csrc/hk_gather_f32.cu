@@ -261,6 +261,52 @@ __device__ __forceinline__ void sweep(const Rec &q, int g0, int g1, int lo_g, in
     }
 }
 
+// The binned Gaussian over groups [g0, g1] with shared bin edges: bin k's
+// value is sbin (F(e_k+1) - F(e_k)), e_k = x_k - b/2 its lower edge, F = erf,
+// taken through E(e) = erfc(|e|) (both edges >= 0: E_lo - E_hi; both <= 0:
+// E_hi - E_lo; straddling the centre: 2 - E_lo - E_hi).  Each lane evaluates
+// E at its bin's lower edge only; the upper edge is the next lane's lower edge
+// (lane 31: the next group's lane 0), so a group is finished one step later
+// and one extra edge closes the pass.  Edge groups gA, gB go through the
+// masked per-bin form.
+template <int V>
+__device__ __forceinline__ void sweep_binned(const Rec &q, int g0, int g1, int lo_g, int hi_g,
+                                             int tg0, float *base, int kfc, int lane)
+{
+    g0 = max(g0, lo_g);
+    g1 = min(g1, hi_g);
+    if (g0 > g1) return;
+    if (g0 == q.gA) {
+        edge_group<kBandBinned, V>(q, g0, tg0, base, kfc, lane);
+        if (++g0 > g1) return;
+    }
+    if (g1 == q.gB) {
+        edge_group<kBandBinned, V>(q, g1, tg0, base, kfc, lane);
+        if (--g1 < g0) return;
+    }
+    // lower edge of this lane's bin in group g: x - b/2
+    auto lower = [&](int g) { return fmaf((float)(32 * g + kfc), q.b, -q.rnb) - q.Yq; };
+    float e = lower(g0);
+    float E = erfcf(fabsf(e));
+    for (int g = g0; g <= g1; ++g) {
+        const float en = lower(g + 1);                 // the next group's lower edges
+        const float En = erfcf(fabsf(en));
+        float eh = __shfl_down_sync(0xffffffffu, e, 1);
+        float Eh = __shfl_down_sync(0xffffffffu, E, 1);
+        const float e0 = __shfl_sync(0xffffffffu, en, 0), E0 = __shfl_sync(0xffffffffu, En, 0);
+        if (lane == 31) {
+            eh = e0;
+            Eh = E0;
+        }
+        const float d = (e >= 0.0f) ? E - Eh : (eh <= 0.0f ? Eh - E : 2.0f - E - Eh);
+        float v = q.sy2 * d;
+        if (V & kVPlinth) v -= q.h;
+        base[32 * (g - tg0)] += v;
+        e = en;
+        E = En;
+    }
+}
+
 __device__ __forceinline__ void core_entry(Smem &S, int warp, int t0, unsigned e)
 {
     const Rec &qq = S.rec[warp][e >> 16];
@@ -330,7 +376,7 @@ __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1
         return;
     }
     if (V & kVBinned) {
-        sweep<kBandBinned, V>(q, q.gA, q.gB, ga, gb, tg0, base, kfc, lane);
+        sweep_binned<V>(q, q.gA, q.gB, ga, gb, tg0, base, kfc, lane);
         return;
     }
     // short lines (no kVPeel): the one-node region takes the two-node rule, one
