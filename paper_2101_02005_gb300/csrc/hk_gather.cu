@@ -136,7 +136,10 @@ __global__ void k_cut_max(const Prob *__restrict__ probs, int nprob, GridD g)
          l += (int64_t)gridDim.x * blockDim.x) {
         const double nu0 = pr.nu0[l], pos = line_pos(pr, l);
         if (!(pos > 0.0)) continue;
-        const CutW cw = line_cut(pr, g, l, nu0);
+        // the float Lorentz width, inflated past its distance to the FP64 one
+        const bool fl = g.cut_mode == kCutLorentz && !(pr.gamma_self && pr.press_air < 0.0);
+        CutW cw = fl ? lorentz_cut_f32(pr, g, l) : line_cut(pr, g, l, nu0);
+        if (fl) cw.W = cw.W * (1.0 + 1e-5) + 1e-3;
         if (cw.nocut) continue;
         // the reach of the line from its unshifted centre: cut plus |shift|
         const double cut = __dmul_rn(cw.W, g.dnu) * (1.0 + 1e-12) + fabs(pos - nu0) * (1.0 + 1e-12) +
@@ -451,9 +454,8 @@ __global__ void k_count_pairs(Prob p, GridD g, unsigned long long *counts)
         // the FP32 kernels' geometry (its pair total must equal the oracle's)
         int cb, lo, hi;
         float rnf;
-        const double nu0 = p.nu0[l];
-        if (!line_geometry_f32(line_pos(p, l), g, line_cut(p, g, l, nu0), &cb, &rnf, &lo, &hi))
-            continue;
+        CutW cw;
+        if (!line_geometry_cut(p, g, l, &cw, &cb, &rnf, &lo, &hi)) continue;
         const double r = (double)rnf;
         double S, aDinv, y;
         line_strength_f64(p, l, &S, &aDinv, &y);

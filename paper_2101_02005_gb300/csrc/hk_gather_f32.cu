@@ -104,8 +104,8 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
     Rec q;
     int c, lo, hi;
     float rn;
-    const CutW cw = line_cut(pr, g, l, pr.nu0[l]);
-    const bool any = line_geometry_f32(line_pos(pr, l), g, cw, &c, &rn, &lo, &hi);
+    CutW cw;
+    const bool any = line_geometry_cut(pr, g, l, &cw, &c, &rn, &lo, &hi);
     q.c = c;
     q.lo = lo;
     q.hi = hi;

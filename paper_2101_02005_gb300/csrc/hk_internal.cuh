@@ -449,9 +449,12 @@ __device__ __forceinline__ bool line_geometry(double nu0, const GridD &g, int *i
 // those lie more than 1e-5 from an integer; otherwise (and for W >= 2^30)
 // from line_geometry's exact FP64 walk.  Also returns the nearest bin c and
 // the offset rn in [-1/2, 1/2] (see nearest_bin) as a float.
-__device__ __forceinline__ bool line_geometry_f32(double nu0, const GridD &g, const CutW &cw,
-                                                  int *c_out, float *rn_out, int *lo_out,
-                                                  int *hi_out)
+// margin: distance from a tie (in bins) below which the FP32 sums cannot
+// decide; walk: take the exact FP64 walk then (else return -1, undecided).
+// Returns 1 if some bin of the grid is inside, 0 if none.
+__device__ __forceinline__ int line_geometry_f32_m(double nu0, const GridD &g, const CutW &cw,
+                                                   float margin, bool walk, int *c_out,
+                                                   float *rn_out, int *lo_out, int *hi_out)
 {
     const double u = __dmul_rn(__dsub_rn(nu0, g.nu_min), g.inv_dnu);
     const double f = floor(u);
@@ -467,12 +470,13 @@ __device__ __forceinline__ bool line_geometry_f32(double nu0, const GridD &g, co
     } else if (cw.Wi >= 0) {
         const float sh = rf + cw.Wf, sl = rf - cw.Wf;
         const float th = sh - rintf(sh), tl = sl - rintf(sl);
-        if (fabsf(th) > 1e-5f && fabsf(tl) > 1e-5f) {
+        if (fabsf(th) > margin && fabsf(tl) > margin) {
             hi = i0 + cw.Wi + (long long)floorf(sh);
             lo = i0 - cw.Wi + (long long)ceilf(sl);
             exact = false;
         }
     }
+    if (exact && !walk) return -1;
     if (exact) {
         int i0e, loe, hie;
         double re;
@@ -489,14 +493,69 @@ __device__ __forceinline__ bool line_geometry_f32(double nu0, const GridD &g, co
         *rn_out = 0.0f;
         *lo_out = 0x3fffffff;
         *hi_out = -0x3fffffff;
-        return false;
+        return 0;
     }
     const bool up = rf >= 0.5f;   // either choice is a valid nearest-bin split
     *c_out = (int)i0 + (up ? 1 : 0);
     *rn_out = (float)(up ? r - 1.0 : r);
     *lo_out = (int)lo;
     *hi_out = (int)hi;
-    return true;
+    return 1;
+}
+
+__device__ __forceinline__ bool line_geometry_f32(double nu0, const GridD &g, const CutW &cw,
+                                                  int *c_out, float *rn_out, int *lo_out,
+                                                  int *hi_out)
+{
+    return line_geometry_f32_m(nu0, g, cw, 1e-5f, true, c_out, rn_out, lo_out, hi_out) == 1;
+}
+
+// The Lorentz-multiple cut from the float Lorentz width (as the FP32 strength
+// forms it): within ~4e-6 relative of the FP64 width of line_cut.
+__device__ __forceinline__ CutW lorentz_cut_f32(const Prob &p, const GridD &g, int64_t l)
+{
+    const float nat = p.A ? p.A[l] * p.nat_coef_f : 0.0f;
+    const float trn = exp2f(p.n_T[l] * p.log2_tratio_f);
+    const float GL = p.gamma_self
+                         ? nat + trn * fmaf(p.gamma[l], p.press_air_f, p.gamma_self[l] * p.press_self_f)
+                         : nat + p.gamma[l] * trn * p.press_f;
+    const float W = (float)g.cut_factor * GL * (float)g.inv_dnu;
+    CutW c;
+    c.nocut = false;
+    c.W = (double)W;
+    if (W >= 0.0f && W < 8388608.0f) {
+        c.Wi = (int)floorf(W);
+        c.Wf = W - (float)c.Wi;
+    } else {
+        c.Wi = -1;
+        c.Wf = 0.0f;
+    }
+    return c;
+}
+
+// FP32-kernel geometry with the line's own cut.  Lorentz-multiple cuts try
+// the float width first, with a tie margin covering its distance to the FP64
+// width (the FP64 pow is slow on this GPU), and take the FP64 width only for
+// a line the float width cannot decide; every other mode is exact at once.
+// cw_out: the width used (its W serves the plinth).
+__device__ __forceinline__ bool line_geometry_cut(const Prob &p, const GridD &g, int64_t l,
+                                                  CutW *cw_out, int *c_out, float *rn_out,
+                                                  int *lo_out, int *hi_out)
+{
+    const double pos = line_pos(p, l);
+    // (with P_self > P the HITRAN width is a difference: no float shortcut)
+    if (g.cut_mode == kCutLorentz && !(p.gamma_self && p.press_air < 0.0)) {
+        const CutW a = lorentz_cut_f32(p, g, l);
+        const float margin = 1e-5f + 4e-6f * (float)a.W;
+        const int res = line_geometry_f32_m(pos, g, a, margin, false, c_out, rn_out, lo_out, hi_out);
+        if (res >= 0) {
+            *cw_out = a;
+            return res == 1;
+        }
+    }
+    const CutW cw = line_cut(p, g, l, p.nu0[l]);
+    *cw_out = cw;
+    return line_geometry_f32(pos, g, cw, c_out, rn_out, lo_out, hi_out);
 }
 
 // Offset of bin i from the line centre in bins, as (i - c) - rn with the
