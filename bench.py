@@ -39,9 +39,9 @@ METRIC = "lines/s and Voigt evals/s on 1 GB300 (FP32-comp vs FP64 GPU) at stated
 # the one-node rule's 8 flops there, so it under-reports rather than inflates.
 FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 25, "gh4": 25, "core": 200}
 # DRAM bytes per line of one k_gather_f32 launch, from the ncu capture in
-# profiles/k_gather_f32_config1-1e7-lines.md (246.7 MB for 1e7 lines; traffic
+# profiles/k_gather_f32_config1-1e7-lines.md (246.2 MB for 1e7 lines; traffic
 # grows with the line count).  Set to None when the kernel changes.
-GATHER_DRAM_BYTES_PER_LINE = 24.67
+GATHER_DRAM_BYTES_PER_LINE = 24.62
 FP32_LANES_PER_SM = 128
 
 
