@@ -398,7 +398,7 @@ def main():
         e2e = {"value": job_rate(L.n, world, ems, args.steps), "unit": "lines/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": ems / args.steps, "call": "hk_cross_section_host",
-               "block_lines": 1 << 23, "clocks": eclocks}
+               "block_lines": 1 << 26, "clocks": eclocks}
         del H
 
     # the plain FP64 GPU form on every 10th line (per-line work is the same

@@ -214,8 +214,9 @@ int hk_cross_section(const hk_lines *lines, const hk_grid *grid, const hk_state 
  * blocks whose copies overlap the sums of the previous block (Sect. 2.3;
  * Sect. 2.4.1, asynchronous interleaved copies of line-list blocks;
  * Sect. 2.4.6 and its workflow figure, copies "C" hidden behind the
- * kernels).  Blocks grow from chunk_lines/8 to chunk_lines lines (0: 2^23,
- * two device buffers of 200 MB for five fields); each is copied on an
+ * kernels).  Blocks grow from chunk_lines/8 to chunk_lines lines (0: 2^26,
+ * two device buffers of 1.6 GB for five fields; a list shorter than that
+ * takes buffers of its own size); each is copied on an
  * internal copy stream into one of two device buffers, then summed exactly
  * as hk_cross_section sums a device-resident list (its own strength, FP32
  * scale and tile schedule) into an FP64 partial sigma.  Even blocks run on

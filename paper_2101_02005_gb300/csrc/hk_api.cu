@@ -681,7 +681,7 @@ int hk_cross_section_host(const hk_lines *lines, const hk_grid *grid, const hk_s
     const int out_f64 = (prec == HK_FP64 || (opts->flags & HK_SIGMA_F64)) ? 1 : 0;
     const int64_t n = lines->n, nbins = grid->nbins;
     const int64_t C = std::max<int64_t>(1, std::min<int64_t>(chunk_lines > 0 ? chunk_lines
-                                                                             : (int64_t)1 << 23,
+                                                                             : (int64_t)1 << 26,
                                                              std::max<int64_t>(n, 1)));
     // float fields present (S_ref, E_low, gamma_ref, n_T, A, g_up, gamma_self, delta)
     const float *hf[8] = {lines->S_ref, lines->E_low, lines->gamma_ref, lines->n_T, lines->A,

@@ -24,7 +24,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import BIN_TOL, L1_TOL, MASK_REL
+from parity import BIN_TOL, L1_TOL, MASK_REL, sigma_errors
 from paper_2101_02005_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -120,10 +120,20 @@ def test_config1_full(hk):
     hk.hk_sync_status()
     sig = sig.cpu().numpy()
     check_sampled(sig, L, w.grid.astuple(), state, w.cut, 11, "c1 fp32c")
-    L10 = L.subset(np.arange(0, L.n, 10))
-    D10 = hk.DeviceLines.from_host(L10)
+    # the benchmark's end-to-end call: the list streamed from page-locked host
+    # memory in the default blocks (2^23 .. 2^26 lines, a ragged last one)
     del D
     _free()
+    H = hk.HostLines.from_host(L)
+    sh = hk.hk_cross_section_host(H, grid, st, hk.make_opts(QREF, w.cut, hk.HK_FP32C,
+                                                            flags=hk.HK_SIGMA_F64))
+    hk.hk_sync_status()
+    del H
+    e = sigma_errors(sh.numpy(), sig)
+    assert e["max_bin"] <= 1e-6, ("c1 host-streamed vs device-resident", e)
+    check_sampled(sh.numpy(), L, w.grid.astuple(), state, w.cut, 13, "c1 fp32c host-streamed")
+    L10 = L.subset(np.arange(0, L.n, 10))
+    D10 = hk.DeviceLines.from_host(L10)
     s64 = hk.hk_cross_section(D10, grid, st, hk.make_opts(QREF, w.cut, hk.HK_FP64))
     hk.hk_sync_status()
     check_sampled(s64.cpu().numpy(), L10, w.grid.astuple(), state, w.cut, 12, "c1 fp64 1/10")
