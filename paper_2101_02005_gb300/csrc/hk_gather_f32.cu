@@ -379,6 +379,21 @@ __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1
         sweep_binned<V>(q, q.gA, q.gB, ga, gb, tg0, base, kfc, lane);
         return;
     }
+    // a tile inside one one-node segment of a wide line, clear of its edge
+    // groups: one unmasked pass and none of the other bands' prologues
+    if ((V & kVPeel) && tg1 < q.gB && ((tg0 > q.gA && tg1 < q.L2) || tg0 > q.R2)) {
+        float kf = (float)(32 * tg0 + kfc);
+        float *p = base;
+        float *const pe = base + 32 * (tg1 - tg0);
+        for (; p < pe; p += 64, kf += 64.0f) {
+            const float v0 = pair_f<kBandGH1, V>(q, kf);
+            const float v1 = pair_f<kBandGH1, V>(q, kf + 32.0f);
+            p[0] += v0;
+            p[32] += v1;
+        }
+        if (p == pe) p[0] += pair_f<kBandGH1, V>(q, kf);
+        return;
+    }
     // short lines (no kVPeel): the one-node region takes the two-node rule, one
     // pass fewer on each side for a few more flops per far-wing pair
     if (V & kVPeel) {
