@@ -239,6 +239,43 @@ def test_line_profiles(hk, prec):
         assert d[m].sum() <= 1e-5 * base[m].sum(), what
 
 
+def test_wide_lines_whole_tiles(hk):
+    """Lines 20001 bins wide (and uncut) on a grid of ~100 tiles, so that
+    most tiles lie wholly inside one one-node segment of a line (the peeled
+    instance's one-pass tiles), next to tiles holding a line's edge groups,
+    its centre, and the grid's ragged end: Voigt, Voigt with the plinth, the
+    Lorentzian (one-node everywhere) with and without the plinth, and no cut,
+    in FP32C against the oracle."""
+    L = synth.make_lines(300, 0.0, 1000.0, synth.SEED_BASE + 11, 18.0)
+    grid = synth.Grid(0.0, 0.01, 100003)
+    T, P = 1000.0, 1.0
+    D = hk.DeviceLines.from_host(L)
+    st = hk.make_state(T, P, float(Q(T)))
+    V, LZ = hk.HK_PROFILE_VOIGT, hk.HK_PROFILE_LORENTZ
+    cases = [(V, hk.HK_CUT_FIXED, 100.0, False), (V, hk.HK_CUT_FIXED, 100.0, True),
+             (LZ, hk.HK_CUT_FIXED, 100.0, False), (LZ, hk.HK_CUT_FIXED, 100.0, True),
+             (V, hk.HK_CUT_NONE, 0.0, False)]
+    for prof, mode, cut, plinth in cases:
+        flags = (hk.HK_REMOVE_PLINTH if plinth else 0) | hk.HK_SIGMA_F64
+        opts = hk.make_opts(QREF, cut, hk.HK_FP32C, cut_mode=mode, flags=flags, profile=prof)
+        got = hk.hk_cross_section(D, hk.make_grid(*grid.astuple()), st, opts)
+        hk.hk_sync_status()
+        got = got.cpu().numpy()
+        args = (L.as_oracle(), grid.astuple(), (T, P, float(Q(T)), QREF), cut)
+        ref = oracle.cross_section(*args, cut_mode=mode, plinth=plinth, profile=prof)
+        what = f"profile={prof} mode={mode} cut={cut} plinth={plinth}"
+        assert np.all(np.isfinite(got)), what
+        assert np.all(got[ref == 0] == 0), what
+        if not plinth:
+            assert_sigma_close(got, ref, what)
+            continue
+        base = oracle.cross_section(*args, cut_mode=mode, plinth=False, profile=prof)
+        m = base > 1e-10 * base.max()
+        d = np.abs(got - ref)
+        assert np.max(d[m] / base[m]) <= 1e-4, what
+        assert d[m].sum() <= 1e-5 * base[m].sum(), what
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_hitran_widths_and_pressure_shift(hk, prec):
     """HITRAN air/self widths (Eq. gammaL) and pressure-shifted positions on a
