@@ -11,7 +11,8 @@
 //   sweeps each line's bins inside the tile, 32 consecutive bins per step
 //   (lane = bin).  Only a line's first and last groups can be partial: the
 //   masked instance tests every group (short lines), the peeled one only
-//   those two (wide lines).
+//   those two (wide lines), and takes a tile that lies wholly inside one
+//   one-node segment of a line in a single unmasked pass.
 // * The Faddeeva band of a 32-bin group is the band of its bin nearest the
 //   line centre.  The bands form nested intervals of group indices around
 //   the centre, computed once per line, so each group runs one formula with
