@@ -360,6 +360,30 @@ def test_backward_rejects_plinth_and_per_line_cuts(hk):
     assert e.value.status == hk.HK_ENOTSUP
 
 
+def test_pool_limit_gives_enomem_and_recovers(hk, monkeypatch):
+    """Host-side allocation failure: with the scratch pool released and its
+    limit (HK_POOL_LIMIT_MB) below what a call needs, the call returns
+    HK_ENOMEM before any device work; with the limit lifted the same call
+    succeeds and matches the oracle (the context stays usable)."""
+    w = synth.config(0, scale=0.1)
+    L = w.species[0]
+    T, P = w.states()[0]
+    D = hk.DeviceLines.from_host(L)
+    grid = hk.make_grid(*w.grid.astuple())
+    st = hk.make_state(T, P, float(Q(T)))
+    opts = hk.make_opts(QREF, w.cut)
+    torch.cuda.synchronize()
+    hk.hk_release()
+    monkeypatch.setenv("HK_POOL_LIMIT_MB", "0.001")
+    with pytest.raises(hk.HKError) as ei:
+        hk.hk_cross_section(D, grid, st, opts)
+    assert ei.value.status == hk.HK_ENOMEM
+    monkeypatch.delenv("HK_POOL_LIMIT_MB")
+    got = hk.hk_cross_section(D, grid, st, opts)
+    hk.hk_sync_status()
+    assert_sigma_close(got.cpu().numpy(), oracle_sigma(L, w.grid, T, P, w.cut), "after ENOMEM")
+
+
 def test_zero_lines_and_single_line(hk):
     L0 = synth.make_lines(0, 0, 10, 1, 18.0)
     grid = synth.Grid(0.0, 0.01, 1000)
