@@ -63,7 +63,8 @@ extern "C" {
                          T <= 0, P < 0, Q <= 0, mass <= 0, NaN, unknown enum) */
 #define HK_ENOMEM 2   /* scratch pool or caller workspace too small */
 #define HK_ECUDA 3    /* a CUDA launch or runtime call failed */
-#define HK_ETIMEOUT 4 /* a bounded device-side wait gave up (see hk_sync_status) */
+#define HK_ETIMEOUT 4 /* a bounded device-side wait gave up (see hk_sync_status); reserved:
+                         no kernel of this version waits on another block or launch */
 #define HK_ENOTSUP 5  /* combination of options not supported */
 #define HK_ERANGE 6   /* a float sigma output overflowed (reported by hk_sync_status);
                          request double output with HK_SIGMA_F64 */
