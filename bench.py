@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="time hk_cross_section_backward over all (T, P) points of the "
                          "workload (config 4) instead of the forward step")
+    ap.add_argument("--batched", action="store_true",
+                    help="time one hk_cross_section_batched launch over every species x "
+                         "(T, P) point of the workload (config 3) per step")
     return ap.parse_args()
 
 
@@ -263,6 +266,75 @@ def run_adjoint(args, w, hk, synth, dev):
                                  "pairs_per_step": pairs}}), flush=True)
 
 
+def run_batched(args, w, hk, synth, dev):
+    """One step = one persistent batched launch over every species at every
+    (T, P) point of the workload (config 3: 4 species x 200 points, sigma in
+    FP64, 12.8 GB); lines per work item from the library's autotuner on the
+    largest species at the middle point.  Pair and band counts (for the cost
+    model) come from hk_count_pairs, outside the timed region."""
+    import torch
+    Q = synth.partition_function
+    species = [hk.DeviceLines.from_host(s) for s in w.species]
+    grid = hk.make_grid(*w.grid.astuple())
+    opts = hk.make_opts(float(Q(296.0)), w.cut, hk.HK_FP32C, flags=hk.HK_SIGMA_F64)
+    pts = w.states()
+    states = [hk.make_state(t, p, float(Q(t))) for t, p in pts]
+    counts = [0] * 6
+    for s in species:
+        for st in states:
+            c = hk.hk_count_pairs(s, grid, st, opts)
+            counts = [a + b for a, b in zip(counts, c)]
+    bands = dict(zip(["gh1", "gh2", "gh3", "gh4", "core"], counts[1:]))
+    flops_step = sum(FLOPS_PER_PAIR[b] * n for b, n in bands.items())
+    big = max(range(len(species)), key=lambda i: species[i].n)
+    hk.hk_autotune(species[big], grid, states[len(states) // 2], opts)
+    lmax = hk.hk_tuning(hk.HK_FP32C)
+    need = hk.hk_workspace_size(0, species, len(states), grid, opts)
+    ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    out = torch.empty((len(species), len(states), w.grid.nbins), dtype=torch.float64, device=dev)
+
+    def step():
+        hk.hk_cross_section_batched(species, states, grid, opts, out, ws)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    hk.hk_sync_status()
+    sampler = ClockSampler(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    sampler.start()
+    time.sleep(0.3)
+    hk.hk_profile(1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    gather_ms, launches = hk.hk_profile(0)
+    clocks = sampler.stop()
+    hk.hk_sync_status()
+    ms = e0.elapsed_time(e1) / args.steps
+    g_ms = gather_ms / max(launches, 1)
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(load_peaks().get("sm_max_mhz", 2070.0))
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = flops_step / (g_ms / 1e3) / 1e12
+    line_points = sum(s.n for s in species) * len(states)
+    print(json.dumps({"metric": "batched line-points/s", "value": line_points / (ms / 1e3),
+                      "unit": "line-points/s", "ms_per_step": ms, "steps": args.steps,
+                      "warmup": args.warmup, "voigt_evals_per_s": counts[0] / (ms / 1e3),
+                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                      "roofline": {"bound": "alu", "kernel": "k_gather_f32", "achieved": achieved,
+                                   "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                                   "gather_ms_per_launch": g_ms, "cost_model": FLOPS_PER_PAIR},
+                      "clocks": clocks,
+                      "config": {"workload": w.name, "species_lines": [s.n for s in species],
+                                 "points": len(states), "pairs_per_step": counts[0],
+                                 "band_pairs": bands, "lmax_autotuned": lmax,
+                                 "sigma_out": "f64"}}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -294,6 +366,9 @@ def main():
     t_gen = time.perf_counter() - t_gen
     if args.adjoint:
         run_adjoint(args, w, hk, synth, dev)
+        return
+    if args.batched:
+        run_batched(args, w, hk, synth, dev)
         return
 
     # line list resident in HBM; pinned host copies for the end-to-end timing
