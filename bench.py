@@ -127,6 +127,26 @@ class ClockSampler:
                 "samples": len(sm), "power_w_max": max(power) if power else None}
 
 
+def smi_gpu_id(dev):
+    """The nvidia-smi id of torch device `dev`: its UUID (GPU-...), which names
+    the same physical GPU whatever CUDA_VISIBLE_DEVICES remaps (nvidia-smi -i
+    ignores that variable); else the physical index taken from that list."""
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        if u:
+            return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    idx = dev.index or 0
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if idx < len(ids):
+            return ids[idx]
+    return str(idx)
+
+
 def workload(args):
     from paper_2101_02005_gb300 import synth
     w = synth.config(args.config, scale=args.scale)
@@ -300,7 +320,7 @@ def run_batched(args, w, hk, synth, dev):
         step()
     torch.cuda.synchronize()
     hk.hk_sync_status()
-    sampler = ClockSampler(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    sampler = ClockSampler(smi_gpu_id(dev))
     sampler.start()
     time.sleep(0.3)
     hk.hk_profile(1)
@@ -403,7 +423,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    sampler = ClockSampler(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    sampler = ClockSampler(smi_gpu_id(dev))
     barrier()
     sampler.start()
     time.sleep(0.3)
@@ -458,7 +478,7 @@ def main():
 
         e2e_step()
         barrier()
-        esampler = ClockSampler(dev.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+        esampler = ClockSampler(smi_gpu_id(dev))
         esampler.start()
         time.sleep(0.3)
         f0 = torch.cuda.Event(enable_timing=True)

@@ -259,9 +259,9 @@ int hk_cross_section_host(const hk_lines *lines, const hk_grid *grid, const hk_s
  * must fit the array: about 2.09e6 bins for HK_FP32C and 2.6e8 for HK_FP64,
  * exactly when hk_cross_section's workspace plus 256 bytes is at most
  * HK_NOALLOC_SCRATCH_BYTES; larger grids return HK_ESIZE before anything is
- * enqueued.  A float output that overflows is not reported (its status flag
- * lives in the array); request HK_SIGMA_F64 when S(T) can exceed the float
- * range.
+ * enqueued.  A float output that overflows sets a status flag inside the
+ * array (not the word hk_sync_status reads): hk_noalloc_status reports it;
+ * request HK_SIGMA_F64 when S(T) can exceed the float range.
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
@@ -274,6 +274,14 @@ int hk_cross_section_host(const hk_lines *lines, const hk_grid *grid, const hk_s
 #define HK_NOALLOC_SCRATCH_BYTES (16u << 20)
 int hk_cross_section_noalloc(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
                              const hk_opts *opts, void *sigma_out, void *stream);
+
+/* Status of the most recent hk_cross_section_noalloc call on the current
+ * device (no paper counterpart): synchronises `stream` (the stream that call
+ * ran on), then returns HK_ERANGE if its float sigma output overflowed, else
+ * 0 (HK_ECUDA on a CUDA error), and clears the flag.  Like the call itself it
+ * allocates no device memory; before any hk_cross_section_noalloc call on the
+ * device it returns 0. */
+int hk_noalloc_status(void *stream);
 
 /* Opacity table in one persistent launch: every species x every (T, P)
  * point (pressure batching of Sect. 2.4.6 / Sect. 3.5, generalised to a T-P
@@ -310,8 +318,9 @@ int hk_workspace_size(int kind, const hk_lines *species, int nspecies, int nTP,
 
 /* The self-tuning of Sect. 2.4.4 (the paper re-tunes its thread counts
  * during a run), done once: times the Voigt sum of this problem for each
- * candidate number of lines per work item (2048 ... 131072; small items
- * balance uneven line density, large ones amortise per-item costs) and
+ * candidate number of lines per work item (1024, 2048, 4096, 16384 and
+ * 65536; small items balance uneven line density, large ones amortise
+ * per-item costs) and
  * caches the fastest for the current device and opts->precision; later
  * calls, batched ones included, use it.  Runs the problem eight times and
  * synchronises `stream`.  Allocates one nbins-sized buffer while it runs. */

@@ -831,6 +831,28 @@ int hk_cross_section_noalloc(const hk_lines *lines, const hk_grid *grid, const h
                       status, st, num_sms());
 }
 
+int hk_noalloc_status(void *stream)
+{
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e) return fail_cuda(e);
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev))) return fail_cuda(e);
+    char *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        auto it = g_noalloc_addr.find(dev);
+        if (it == g_noalloc_addr.end()) return HK_OK;   // no call on this device yet
+        scratch = it->second;
+    }
+    unsigned v = 0;
+    e = cudaMemcpy(&v, scratch, sizeof(v), cudaMemcpyDeviceToHost);
+    if (!e && v) e = cudaMemset(scratch, 0, sizeof(v));
+    if (e) return fail_cuda(e);
+    if (v & kStatusTimeout) return HK_ETIMEOUT;
+    if (v & kStatusRange) return HK_ERANGE;
+    return HK_OK;
+}
+
 int hk_workspace_size(int kind, const hk_lines *species, int nspecies, int nTP,
                       const hk_grid *grid, const hk_opts *opts, size_t *bytes)
 {
@@ -967,9 +989,15 @@ int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *stat
         (void)cudaGetLastError();
         return HK_ENOMEM;
     }
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (!ce) ce = cudaEventCreate(&e1);
+    if (ce) {
+        rc = fail_cuda(ce);
+        if (e0) cudaEventDestroy(e0);
+        cudaFree(out);
+        return rc;
+    }
     hk_opts o = *opts;
     o.flags |= HK_SIGMA_F64;  // time without any float-overflow concern
     Tune best = get_tune(prec);
@@ -977,16 +1005,18 @@ int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *stat
     for (int j = 0; j < ncand && rc == HK_OK; ++j) {
         rc = cross_section_impl(lines, grid, state, &o, out, st, bpt, lmaxs[j]);  // warm-up
         if (rc) break;
-        cudaEventRecord(e0, st);
-        rc = cross_section_impl(lines, grid, state, &o, out, st, bpt, lmaxs[j]);
-        cudaEventRecord(e1, st);
-        if (rc) break;
-        if (cudaEventSynchronize(e1) != cudaSuccess) {
-            rc = fail_cuda(cudaGetLastError());
+        if ((ce = cudaEventRecord(e0, st))) {
+            rc = fail_cuda(ce);
             break;
         }
+        rc = cross_section_impl(lines, grid, state, &o, out, st, bpt, lmaxs[j]);
+        if (rc) break;
         float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
+        if ((ce = cudaEventRecord(e1, st)) || (ce = cudaEventSynchronize(e1)) ||
+            (ce = cudaEventElapsedTime(&ms, e0, e1))) {
+            rc = fail_cuda(ce);
+            break;
+        }
         if (ms < best_ms) {
             best_ms = ms;
             best.bpt = bpt;
@@ -995,8 +1025,10 @@ int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *stat
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaStreamSynchronize(st);
-    cudaFree(out);
+    ce = cudaStreamSynchronize(st);
+    if (ce && !rc) rc = fail_cuda(ce);
+    ce = cudaFree(out);
+    if (ce && !rc) rc = fail_cuda(ce);
     if (rc) return rc;
     int dev = 0;
     cudaGetDevice(&dev);

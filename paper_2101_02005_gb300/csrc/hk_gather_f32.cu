@@ -29,6 +29,8 @@
 
 #include <climits>
 #include <cstdint>
+#include <map>
+#include <mutex>
 
 #include "hk_internal.cuh"
 #include "hk_launch.h"
@@ -526,25 +528,45 @@ size_t gather_f32_smem() { return sizeof(f32g::Smem); }
 // Lines at least this many bins wide take the peeled sweeps.
 constexpr double kPeelBins = 1024.0;
 
+// Blocks per SM of a kernel instance on the current device, after raising its
+// dynamic shared-memory limit there (a per-device attribute): done once per
+// (device, instance) under a lock, so concurrent first calls from several host
+// threads, or a second device, each see a configured kernel.
+static int configure_once(const void *fn, size_t smem, int threads, int *per_sm_out)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, int> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return fail_cuda(e);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = done.find({dev, fn});
+    if (it != done.end()) {
+        *per_sm_out = it->second;
+        return HK_OK;
+    }
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e) return fail_cuda(e);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    if (e) return fail_cuda(e);
+    if (per_sm < 1) per_sm = 1;
+    done[{dev, fn}] = per_sm;
+    *per_sm_out = per_sm;
+    return HK_OK;
+}
+
 template <int V>
 static int launch_variant(const Prob *probs_d, const GridD &g, int64_t ntiles, int64_t m,
                           const int64_t *item_off, const int64_t *tile_lb,
                           const int64_t *tile_le, int lmax, unsigned long long *counter,
                           cudaStream_t st, int num_sms)
 {
-    static bool configured = false;
-    static int per_sm = 0;
+    int per_sm = 0;
+    int rc = configure_once((const void *)f32g::k_gather_f32<V>, sizeof(f32g::Smem), f32g::NT,
+                            &per_sm);
+    if (rc) return rc;
     cudaError_t e;
-    if (!configured) {
-        e = cudaFuncSetAttribute(f32g::k_gather_f32<V>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(f32g::Smem));
-        if (e) return fail_cuda(e);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32g::k_gather_f32<V>,
-                                                          f32g::NT, sizeof(f32g::Smem));
-        if (e || per_sm < 1) per_sm = 1;
-        configured = true;
-    }
     f32g::k_gather_f32<V><<<num_sms * per_sm, f32g::NT, sizeof(f32g::Smem), st>>>(
         probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter);
     e = cudaGetLastError();

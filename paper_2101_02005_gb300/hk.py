@@ -29,7 +29,8 @@ EXPORTS = ["hk_line_strength", "hk_widths", "hk_voigt_accumulate", "hk_cross_sec
            "hk_cross_section_batched", "hk_cross_section_backward", "hk_workspace_size",
            "hk_autotune", "hk_sync_status", "hk_release", "hk_strerror", "hk_last_cuda_error",
            "hk_constants", "hk_version", "hk_count_pairs", "hk_profile",
-           "hk_cross_section_noalloc", "hk_tuning", "hk_cross_section_host", "hk_set_tuning"]
+           "hk_cross_section_noalloc", "hk_tuning", "hk_cross_section_host", "hk_set_tuning",
+           "hk_noalloc_status"]
 
 
 class hk_lines(ctypes.Structure):
@@ -105,6 +106,7 @@ def lib():
                                            vp, vp]
     L.hk_cross_section_host.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts), vp,
                                         ctypes.c_int64, vp]
+    L.hk_noalloc_status.argtypes = [vp]
     _lib = L
     return L
 
@@ -116,6 +118,23 @@ def _check(fn, status):
 
 def _ptr(t: Optional[torch.Tensor]):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_out(fn, t: torch.Tensor, numel: int, dtype, device=None, host_ok=False):
+    """Rejects an output tensor the library would write past or misread: wrong
+    element type, too few elements, not contiguous, or on the wrong device
+    (the library trusts the pointer it is given)."""
+    if t.dtype != dtype:
+        raise ValueError(f"{fn}: output dtype {t.dtype}, expected {dtype}")
+    if t.numel() < numel:
+        raise ValueError(f"{fn}: output has {t.numel()} elements, needs {numel}")
+    if not t.is_contiguous():
+        raise ValueError(f"{fn}: output must be contiguous")
+    if t.is_cuda:
+        if device is not None and t.device != device:
+            raise ValueError(f"{fn}: output on {t.device}, lines on {device}")
+    elif not host_ok:
+        raise ValueError(f"{fn}: output must be a CUDA tensor")
 
 
 def _stream(stream=None):
@@ -237,6 +256,8 @@ def hk_widths(lines: DeviceLines, state: hk_state, opts: hk_opts, stream=None):
 
 def hk_voigt_accumulate(nu0, S, alphaD_inv, y, grid: hk_grid, cut: float, sigma_inout,
                         precision=HK_FP32C, stream=None):
+    _check_out("hk_voigt_accumulate", sigma_inout, grid.nbins,
+               torch.float64 if precision == HK_FP64 else torch.float32, nu0.device)
     _check("hk_voigt_accumulate",
            lib().hk_voigt_accumulate(_ptr(nu0), _ptr(S), _ptr(alphaD_inv), _ptr(y), nu0.numel(),
                                      ctypes.byref(grid), float(cut), _ptr(sigma_inout),
@@ -248,6 +269,7 @@ def hk_cross_section(lines: DeviceLines, grid: hk_grid, state: hk_state, opts: h
                      sigma_out=None, stream=None):
     if sigma_out is None:
         sigma_out = torch.empty(grid.nbins, dtype=sigma_dtype(opts), device=lines.nu0.device)
+    _check_out("hk_cross_section", sigma_out, grid.nbins, sigma_dtype(opts), lines.nu0.device)
     L = lines.struct()
     _check("hk_cross_section", lib().hk_cross_section(ctypes.byref(L), ctypes.byref(grid),
                                                       ctypes.byref(state), ctypes.byref(opts),
@@ -263,6 +285,7 @@ def hk_cross_section_host(lines: HostLines, grid: hk_grid, state: hk_state, opts
     synchronised."""
     if sigma_out is None:
         sigma_out = torch.empty(grid.nbins, dtype=sigma_dtype(opts), pin_memory=True)
+    _check_out("hk_cross_section_host", sigma_out, grid.nbins, sigma_dtype(opts), host_ok=True)
     L = lines.struct()
     _check("hk_cross_section_host",
            lib().hk_cross_section_host(ctypes.byref(L), ctypes.byref(grid), ctypes.byref(state),
@@ -275,6 +298,8 @@ def hk_cross_section_noalloc(lines: DeviceLines, grid: hk_grid, state: hk_state,
                              sigma_out: torch.Tensor, stream=None):
     """hk_cross_section with its scratch in the library's fixed device array:
     no device allocation by the library (the caller provides sigma_out)."""
+    _check_out("hk_cross_section_noalloc", sigma_out, grid.nbins, sigma_dtype(opts),
+               lines.nu0.device)
     L = lines.struct()
     _check("hk_cross_section_noalloc",
            lib().hk_cross_section_noalloc(ctypes.byref(L), ctypes.byref(grid),
@@ -300,6 +325,8 @@ def hk_cross_section_batched(species: Sequence[DeviceLines], states: Sequence[hk
     if sigma_out is None:
         sigma_out = torch.empty((len(species), len(states), grid.nbins), dtype=sigma_dtype(opts),
                                 device=dev)
+    _check_out("hk_cross_section_batched", sigma_out, len(species) * len(states) * grid.nbins,
+               sigma_dtype(opts), dev)
     need = hk_workspace_size(0, species, len(states), grid, opts)
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
@@ -377,6 +404,12 @@ def hk_sync_status(stream=None):
     _check("hk_sync_status", lib().hk_sync_status(_stream(stream)))
 
 
+def hk_noalloc_status(stream=None):
+    """Raises HKError(HK_ERANGE) if the latest hk_cross_section_noalloc call
+    on this device overflowed its float output (clears the flag)."""
+    _check("hk_noalloc_status", lib().hk_noalloc_status(_stream(stream)))
+
+
 def hk_release():
     _check("hk_release", lib().hk_release())
 
@@ -395,9 +428,11 @@ def hk_version() -> int:
 
 
 class CrossSectionFn(torch.autograd.Function):
-    """sigma[k] for (T[k], P[k]) points of one species, differentiable in T, P
-    (per point) and S_ref, gamma_ref (per line).  Forward: hk_cross_section_batched
-    (FP32C); backward: hk_cross_section_backward (recomputes the profiles)."""
+    """sigma[k] for (T[k], P[k]) points of one species, as a [points, nbins]
+    tensor differentiable in T, P (per point) and S_ref, gamma_ref (per line).
+    Forward: hk_cross_section_batched (FP32C); backward:
+    hk_cross_section_backward (recomputes the profiles).  Call as
+    CrossSectionFn.apply(T, P, S_ref, gamma_ref, lines, grid, opts, Q_fn, dlnQ_fn)."""
 
     @staticmethod
     def forward(ctx, T, P, S_ref, gamma_ref, lines: DeviceLines, grid: hk_grid, opts: hk_opts,
@@ -408,13 +443,16 @@ class CrossSectionFn(torch.autograd.Function):
         L = DeviceLines(lines.nu0, S_ref.detach().contiguous(), lines.E_low,
                         gamma_ref.detach().contiguous(), lines.n_T, lines.mass_amu, A=lines.A,
                         g_up=lines.g_up, s_mode=lines.s_mode, sorted=lines.sorted)
-        sigma = hk_cross_section_batched([L], states, grid, opts)[0]
+        sigma = hk_cross_section_batched([L], states, grid, opts)
         ctx.L, ctx.states, ctx.grid, ctx.opts = L, states, grid, opts
-        return sigma
+        ctx.tp = (T.dtype, T.device, P.dtype, P.device)
+        return sigma.reshape(len(states), grid.nbins)
 
     @staticmethod
     def backward(ctx, g):
         dT, dP, dS, dG = hk_cross_section_backward(ctx.L, ctx.grid, ctx.states, ctx.opts,
                                                    g.to(torch.float32).contiguous())
-        return (dT.to(torch.float64), dP.to(torch.float64), dS.to(ctx.L.S_ref.dtype),
-                dG.to(ctx.L.gamma_ref.dtype), None, None, None, None, None)
+        tdt, tdev, pdt, pdev = ctx.tp
+        return (dT.to(device=tdev, dtype=tdt), dP.to(device=pdev, dtype=pdt),
+                dS.to(ctx.L.S_ref.dtype), dG.to(ctx.L.gamma_ref.dtype),
+                None, None, None, None, None)
