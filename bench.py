@@ -41,7 +41,7 @@ FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 25, "gh4": 25, "core": 200}
 # DRAM bytes per line of one k_gather_f32 launch, from the ncu capture in
 # profiles/k_gather_f32_config1-1e7-lines.md (246.2 MB for 1e7 lines; traffic
 # grows with the line count).  Set to None when the kernel changes.
-GATHER_DRAM_BYTES_PER_LINE = 24.62
+GATHER_DRAM_BYTES_PER_LINE = None
 FP32_LANES_PER_SM = 128
 
 
@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="time hk_cross_section_backward over all (T, P) points of the "
                          "workload (config 4) instead of the forward step")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched config-3 launch that follows the headline step")
     ap.add_argument("--batched", action="store_true",
                     help="time one hk_cross_section_batched launch over every species x "
                          "(T, P) point of the workload (config 3) per step")
@@ -147,50 +149,106 @@ def smi_gpu_id(dev):
     return str(idx)
 
 
+def measure_peaks(hk, dev, ms=1000.0):
+    """Measured pipe throughputs of this GPU (hk_measure_peak), each with the
+    SM clock sampled while it ran: FP32 FMA, MUFU reciprocal, FP64 FMA."""
+    out = {}
+    for kind, name in [(hk.PEAK_FFMA, "ffma"), (hk.PEAK_RCP, "mufu_rcp"), (hk.PEAK_DFMA, "dfma")]:
+        hk.hk_measure_peak(kind, 100.0)
+        s = ClockSampler(smi_gpu_id(dev))
+        s.start()
+        time.sleep(0.25)
+        v = hk.hk_measure_peak(kind, ms)
+        c = s.stop()
+        out[name] = {"ops_per_s": v, "sm_mhz": c.get("sm_mhz"), "reasons": c.get("reasons")}
+    return out
+
+
+def alu_roofline(flops, g_ms, peaks, props, sm_max):
+    """Cost-model FLOP/s of the gather against the measured FP32 FMA peak
+    (2 flops per FMA), with the nominal unit-count figure beside it."""
+    achieved = flops / (g_ms / 1e3) / 1e12
+    f = peaks["ffma"]
+    peak = 2.0 * f["ops_per_s"] / 1e12
+    nominal = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak,
+            "peak_basis": f"measured FP32 FMA throughput (hk_measure_peak, {f['ops_per_s']:.4g} "
+                          f"FMA/s at {f['sm_mhz']} MHz SM clock), x 2 flops",
+            "peak_nominal": nominal, "frac_of_nominal": achieved / nominal}
+
+
 def workload(args):
     from paper_2101_02005_gb300 import synth
     w = synth.config(args.config, scale=args.scale)
     return w
 
 
-def cpu_sample(w, L, T, P, seconds_target=15.0, nthreads=0):
-    """Times the FP64 oracle (as it stands) on windows of the grid, growing the
-    sample until it has taken ~seconds_target; returns pairs/s, the windows and
-    the oracle's sigma on them."""
+def cpu_sample(w, L, T, P, seconds_target=15.0, nthreads=0, nwin=8):
+    """Times the FP64 oracle (as it stands) on nwin seeded windows of the grid:
+    the densest, the median and the sparsest 100 cm^-1 log-normal window and
+    uniformly drawn positions, each window as many bins wide as takes about
+    seconds_target / nwin of oracle time at its own line density (a bin of the
+    densest config-1 window already holds ~1e7 pairs), every line within the
+    cut of a window included.  Returns pairs/s over all windows, the time, the
+    pairs and the windows (lo, hi, oracle sigma, seconds, pairs)."""
     import oracle
     from paper_2101_02005_gb300 import synth
     Q = synth.partition_function
     grid = w.grid.astuple()
+    nb = w.grid.nbins
     state = (T, P, float(Q(T)), float(Q(296.0)))
-    # windows at the median-density 100 cm^-1 window of the list
+    starts = []
     counts = synth.lognormal_window_counts(L.n, 300, synth.SEED_BASE + w_seed_offset(w)) \
-        if L.n >= 300 else None
-    if counts is not None and w.grid.nbins >= 3000:
-        med = int(np.argsort(counts)[len(counts) // 2])
-        start = med * (w.grid.nbins // 300) + 50
-    else:
-        start = w.grid.nbins // 2
-    width = 16
-    t_used = 0.0
-    pairs = 0
-    wins = []
-    while t_used < seconds_target and width <= 4096:
-        lo, hi = start, min(w.grid.nbins, start + width)
-        # pairs inside this window: lines whose cut range overlaps it
+        if L.n >= 300 and nb >= 3000 else None
+    if counts is not None:
+        order = np.argsort(counts)
+        nz = order[counts[order] > 0]
+        for widx in (order[-1], order[len(order) // 2], nz[0] if nz.size else order[0]):
+            starts.append(int(widx) * (nb // 300) + (nb // 600))
+    rng = np.random.default_rng(synth.SEED_BASE + 77)
+    while len(starts) < nwin:
+        starts.append(int(rng.integers(0, nb)))
+
+    def pairs_in(lo, hi):
         sel = np.searchsorted(L.nu0, [grid[0] + lo * grid[1] - w.cut - grid[1],
                                       grid[0] + hi * grid[1] + w.cut + grid[1]])
         sub = L.subset(slice(int(sel[0]), int(sel[1])))
         rlo, rhi = oracle.line_ranges(sub.nu0, *grid, w.cut)
-        n_pairs = int(np.clip(np.minimum(rhi, hi - 1) - np.maximum(rlo, lo) + 1, 0, None).sum())
+        n = int(np.clip(np.minimum(rhi, hi - 1) - np.maximum(rlo, lo) + 1, 0, None).sum())
+        return sub, n
+
+    # oracle pairs/s from a small probe, to size the windows
+    sub, n = pairs_in(starts[1] if len(starts) > 1 else starts[0],
+                      (starts[1] if len(starts) > 1 else starts[0]) + 1)
+    t0 = time.perf_counter()
+    oracle.cross_section(sub.as_oracle(), grid, state, w.cut, starts[1], starts[1] + 1,
+                         nthreads=nthreads)
+    rate0 = max(n, 1) / max(time.perf_counter() - t0, 1e-4)
+    target = rate0 * seconds_target / nwin
+    t_used, pairs, wins = 0.0, 0, []
+    for st in starts:
+        lo = min(max(st, 0), nb - 1)
+        _, per_bin = pairs_in(lo, lo + 1)
+        width = int(min(2000, max(1, target // max(per_bin, 1))))
+        sub, n_pairs = pairs_in(lo, min(nb, lo + width))
+        while width > 1 and n_pairs > 1.5 * target:   # a denser neighbour within the cut
+            width //= 2
+            sub, n_pairs = pairs_in(lo, min(nb, lo + width))
+        hi = min(nb, lo + width)
         t0 = time.perf_counter()
         ref = oracle.cross_section(sub.as_oracle(), grid, state, w.cut, lo, hi, nthreads=nthreads)
         dt = time.perf_counter() - t0
         t_used += dt
         pairs += n_pairs
         wins.append((lo, hi, ref, dt, n_pairs))
-        start = hi
-        width *= 2
     return pairs / max(t_used, 1e-9), t_used, pairs, wins
+
+
+def sample_text(wins, pairs, secs):
+    return (f"{len(wins)} seeded windows (densest, median and sparsest 100 cm^-1 log-normal "
+            f"window, uniform positions) of " + ", ".join(str(hi - lo) for lo, hi, *_ in wins) +
+            f" bins: {pairs} pairs in {secs:.1f} s, pairs/s extrapolated to the whole list")
 
 
 def max_over_ranks(ms_local, dist, device):
@@ -234,8 +292,7 @@ def run_reference(args):
         rate, secs, pairs, wins = cpu_sample(w, L, T, P, seconds_target=4.0)
         if s >= args.warmup:
             rates.append(rate)
-        sample = (f"bins {wins[0][0]}-{wins[-1][1]} of the median-density window, "
-                  f"{pairs} pairs in {secs:.1f} s per step")
+        sample = sample_text(wins, pairs, secs) + " (per step)"
     rate = statistics.median(rates)
     value = rate / pairs_per_line
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "lines/s",
@@ -287,6 +344,13 @@ def run_adjoint(args, w, hk, synth, dev):
 
 
 def run_batched(args, w, hk, synth, dev):
+    """Prints the batched measurement of the workload as its own JSON line."""
+    peaks = measure_peaks(hk, dev)
+    print(json.dumps(batched_measure(w, hk, synth, dev, args.steps, args.warmup, peaks)),
+          flush=True)
+
+
+def batched_measure(w, hk, synth, dev, steps, warmup, peaks):
     """One step = one persistent batched launch over every species at every
     (T, P) point of the workload (config 3: 4 species x 200 points, sigma in
     FP64, 12.8 GB); lines per work item from the library's autotuner on the
@@ -316,7 +380,7 @@ def run_batched(args, w, hk, synth, dev):
     def step():
         hk.hk_cross_section_batched(species, states, grid, opts, out, ws)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     hk.hk_sync_status()
@@ -327,32 +391,33 @@ def run_batched(args, w, hk, synth, dev):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record()
     torch.cuda.synchronize()
     gather_ms, launches = hk.hk_profile(0)
     clocks = sampler.stop()
     hk.hk_sync_status()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     g_ms = gather_ms / max(launches, 1)
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(load_peaks().get("sm_max_mhz", 2070.0))
-    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    achieved = flops_step / (g_ms / 1e3) / 1e12
+    roof = alu_roofline(flops_step, g_ms, peaks, props, sm_max)
+    roof.update({"kernel": "k_gather_f32", "gather_ms_per_launch": g_ms,
+                 "cost_model": FLOPS_PER_PAIR})
     line_points = sum(s.n for s in species) * len(states)
-    print(json.dumps({"metric": "batched line-points/s", "value": line_points / (ms / 1e3),
-                      "unit": "line-points/s", "ms_per_step": ms, "steps": args.steps,
-                      "warmup": args.warmup, "voigt_evals_per_s": counts[0] / (ms / 1e3),
-                      "higher_is_better": True, "dtype": "f32", "data": "synthetic",
-                      "roofline": {"bound": "alu", "kernel": "k_gather_f32", "achieved": achieved,
-                                   "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                                   "gather_ms_per_launch": g_ms, "cost_model": FLOPS_PER_PAIR},
-                      "clocks": clocks,
-                      "config": {"workload": w.name, "species_lines": [s.n for s in species],
-                                 "points": len(states), "pairs_per_step": counts[0],
-                                 "band_pairs": bands, "lmax_autotuned": lmax,
-                                 "sigma_out": "f64"}}), flush=True)
+    out_ = {"metric": "batched line-points/s", "value": line_points / (ms / 1e3),
+            "unit": "line-points/s", "ms_per_step": ms, "steps": steps,
+            "warmup": warmup, "voigt_evals_per_s": counts[0] / (ms / 1e3),
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "roofline": roof, "clocks": clocks,
+            "config": {"workload": w.name, "species_lines": [s.n for s in species],
+                       "points": len(states), "pairs_per_step": counts[0],
+                       "band_pairs": bands, "lmax_autotuned": lmax,
+                       "sigma_out": "f64", "call": "hk_cross_section_batched"}}
+    del out, ws, species
+    torch.cuda.empty_cache()
+    return out_
 
 
 def main():
@@ -378,6 +443,7 @@ def main():
     pbuild.build()
     from paper_2101_02005_gb300 import hk, synth
 
+    peaks_m = measure_peaks(hk, dev)
     t_gen = time.perf_counter()
     w = workload(args)
     L = w.species[0]
@@ -388,7 +454,8 @@ def main():
         run_adjoint(args, w, hk, synth, dev)
         return
     if args.batched:
-        run_batched(args, w, hk, synth, dev)
+        print(json.dumps(batched_measure(w, hk, synth, dev, args.steps, args.warmup, peaks_m)),
+              flush=True)
         return
 
     # line list resident in HBM; pinned host copies for the end-to-end timing
@@ -443,22 +510,21 @@ def main():
     ms_step = ms_max / args.steps
     value = job_rate(L.n, world, ms_max, args.steps)
 
-    # roofline of the dominant kernel (the Voigt gather), live CUDA-event time
-    peaks = load_peaks()
+    # roofline of the dominant kernel (the Voigt gather), live CUDA-event time,
+    # against the FP32 FMA peak measured on this GPU at the start of the run
     props = torch.cuda.get_device_properties(dev)
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sm_max = float(load_peaks().get("sm_max_mhz", 2070.0))
     g_ms = gather_ms / max(gather_launches, 1)
-    achieved = flops_step / (g_ms / 1e3) / 1e12
     traffic = (GATHER_DRAM_BYTES_PER_LINE * L.n
                if GATHER_DRAM_BYTES_PER_LINE and args.config == 1 else None)
-    roofline = {"bound": "alu", "kernel": "k_gather_f32<false>" if 2 * w.cut / w.grid.dnu + 1 < 1024 else "k_gather_f32<true>", "achieved": achieved,
-                "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                "traffic": traffic, "algorithmic_bytes": 24 * L.n, "gather_ms_per_launch": g_ms,
-                "gather_share_of_step": g_ms / ms_step if ms_step else None,
-                "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
-                              f"{sm_max:.0f} MHz (derived, FP32 FMA)",
-                "flops_per_step": flops_step, "cost_model": FLOPS_PER_PAIR}
+    roofline = alu_roofline(flops_step, g_ms, peaks_m, props, sm_max)
+    roofline.update({
+        "kernel": ("k_gather_f32<0> (batched short-line sweeps)"
+                   if 2 * w.cut / w.grid.dnu + 1 < 1024 else "k_gather_f32<1> (peeled sweeps)"),
+        "traffic": traffic, "algorithmic_bytes": 24 * L.n, "gather_ms_per_launch": g_ms,
+        "gather_share_of_step": g_ms / ms_step if ms_step else None,
+        "flops_per_step": flops_step, "cost_model": FLOPS_PER_PAIR,
+        "measured_peaks": peaks_m})
 
     # end to end through the host-buffer entry point: the line list in pinned
     # host memory is streamed to the GPU in blocks whose copies overlap the
@@ -521,6 +587,20 @@ def main():
                 "sample": "every 10th line of the list, one step"}
         del D64, s64
 
+    # the batched opacity table (config 3: 4 species x 200 (T, P) points in one
+    # persistent launch, FP32C), reported beside the headline; its line list
+    # replaces the headline's on the device
+    batched = None
+    if not args.no_batched and rank == 0 and args.config == 1 and args.scale == 1.0:
+        got_sigma = sigma.cpu().numpy()
+        del D, sigma
+        torch.cuda.empty_cache()
+        w3 = synth.config(3)
+        batched = batched_measure(w3, hk, synth, dev, 1, 1, peaks_m)
+        del w3
+    else:
+        got_sigma = None
+
     # CPU baseline (oracle as it stands, host cores) on a bounded sample, which
     # doubles as a parity check of this run's sigma on the same bins
     cpu = None
@@ -532,9 +612,8 @@ def main():
         pairs_per_line = pairs / L.n
         cpu = {"value": rate / pairs_per_line, "unit": "lines/s", "cores": os.cpu_count(),
                "kind": "oracle", "voigt_evals_per_s": rate,
-               "sample": f"bins {wins[0][0]}-{wins[-1][1]} of the median-density 100 cm^-1 "
-                         f"window, {cpairs} pairs in {secs:.1f} s, extrapolated to the list"}
-        got = sigma.cpu().numpy()
+               "sample": sample_text(wins, cpairs, secs), "extrapolated": True}
+        got = got_sigma if got_sigma is not None else sigma.cpu().numpy()
         errs = [sigma_errors_window(got[lo:hi], ref) for lo, hi, ref, _, _ in wins]
         parity = {"rel_l1_max": max(e["l1"] for e in errs),
                   "max_bin_rel": max(e["max_bin"] for e in errs),
@@ -558,7 +637,7 @@ def main():
                 # ranges, scan, gather, finalize (see the launch list profile)
                 "gpu_launches": 6 * args.steps,
                 "roofline": roofline, "clocks": clocks, "e2e": e2e, "fp64_gpu": fp64,
-                "cpu_baseline": cpu, "parity_sample": parity}
+                "cpu_baseline": cpu, "parity_sample": parity, "batched_c3": batched}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

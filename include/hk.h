@@ -355,6 +355,16 @@ int hk_count_pairs(const hk_lines *lines, const hk_grid *grid, const hk_state *s
  * of launches in *launches (either pointer may be NULL). */
 int hk_profile(int mode, double *ms, int64_t *launches);
 
+/* Instrumentation (no counterpart in the paper): the measured throughput of
+ * one pipe of the current device, for the rooflines of the kernels.  kind 0:
+ * FP32 fused multiply-adds per second; 1: MUFU reciprocals (rcp.approx.ftz)
+ * per second; 2: MUFU base-2 exponentials (ex2.approx.ftz) per second; 3: FP64
+ * fused multiply-adds per second.  Every SM runs 64 warps of independent
+ * chains of the operation; a calibration launch sizes launches of ~100 ms,
+ * repeated for about target_ms (0 < target_ms <= 60000).  *ops_per_s: HOST
+ * double.  Synchronises `stream`; uses the scratch pool (2.5 MB). */
+int hk_measure_peak(int kind, double target_ms, double *ops_per_s, void *stream);
+
 /* Synchronises `stream`, then reports and clears the device status word of
  * the current device: HK_ERANGE if a float sigma output overflowed since the
  * last call, HK_ETIMEOUT if a bounded device wait gave up; HK_ECUDA on a CUDA

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libhk.so")
-SOURCES = ["hk_api.cu", "hk_gather.cu", "hk_gather_f32.cu", "hk_backward.cu"]
+SOURCES = ["hk_api.cu", "hk_gather.cu", "hk_gather_f32.cu", "hk_backward.cu", "hk_peaks.cu"]
 HEADERS = ["hk_internal.cuh", "hk_launch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -1037,6 +1037,49 @@ int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *stat
     return HK_OK;
 }
 
+int hk_measure_peak(int kind, double target_ms, double *ops_per_s, void *stream)
+{
+    if (kind < 0 || kind > 3 || !ops_per_s || !(target_ms > 0.0) || target_ms > 60000.0)
+        return HK_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int sms = num_sms();
+    char *scratch;
+    int rc = pool_get((size_t)sms * 8 * 256 * sizeof(double), &scratch);
+    if (rc) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (!e) e = cudaEventCreate(&e1);
+    double ops = 0.0, total_ops = 0.0;
+    float ms = 0.0f;
+    int iters = 256;
+    // calibration launch (also the warm-up), then launches of ~100 ms each
+    if (!e && !(rc = peak_launch(kind, iters, sms, scratch, &ops, st))) {
+        if (!(e = cudaEventRecord(e0, st)) &&
+            !(rc = peak_launch(kind, iters, sms, scratch, &ops, st)) &&
+            !(e = cudaEventRecord(e1, st)) && !(e = cudaEventSynchronize(e1)) &&
+            !(e = cudaEventElapsedTime(&ms, e0, e1))) {
+            // at most 2000x the calibration launch, so a launch stays bounded
+            const double scale = std::min(100.0 / std::max((double)ms, 1e-3), 2000.0);
+            iters = (int)std::max(iters * scale, 256.0);
+            const int reps = std::max(1, (int)std::ceil(target_ms / 100.0));
+            if (!(e = cudaEventRecord(e0, st))) {
+                for (int r = 0; r < reps && !rc; ++r) {
+                    rc = peak_launch(kind, iters, sms, scratch, &ops, st);
+                    total_ops += ops;
+                }
+                if (!rc && !(e = cudaEventRecord(e1, st)) && !(e = cudaEventSynchronize(e1)))
+                    e = cudaEventElapsedTime(&ms, e0, e1);
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (e) return fail_cuda(e);
+    *ops_per_s = total_ops / (ms * 1e-3);
+    return HK_OK;
+}
+
 int hk_tuning(int precision, int *lmax)
 {
     if ((precision != HK_FP32C && precision != HK_FP64) || !lmax) return HK_EINVAL;

@@ -415,6 +415,344 @@ __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1
     }
 }
 
+// ---- batches of co-located lines (short lines, Voigt, no plinth) --------------
+//
+// In a dense sorted list, consecutive lines share their nearest bin and so
+// their group structure: the same first and last groups (gA, gB)
+// and band boundaries inside the same few central groups.  For NLB such lines
+// the warp takes each group once and sums the lines' values in a register,
+// updating the tile copy once per group instead of once per line.  The
+// groups strictly between gA and the batch's first four-node group (and
+// between its last one and gB) run the two-node rule with no mask and no
+// band test; gA and gB run it with each line's lane mask; the central groups
+// [min L4, max R4] run the four-node rule per line, core bins (r2 < 64)
+// going to the core queue.  x is formed exactly as on the per-line path (the
+// two-node rule is the same rational function, regrouped in X = x^2).  A
+// batch whose lines differ in gA, gB or the nearest bin c, or whose central
+// groups reach gA or gB, takes the per-line path.
+constexpr int NLB = 4;
+
+// Two-node value of a pair, as fma(num, 1/d, acc): with X = x^2,
+// d = |z^2 - 1/2|^2 = X^2 + (2Y - 1) X + (Y + 1/2)^2, num = sy (X + Y + 1/2).
+__device__ __forceinline__ float gh2_acc(float kf, float b, float nrb, float B, float C, float sy,
+                                         float E, float acc)
+{
+    const float x = fmaf(kf, b, nrb);
+    const float X = x * x;
+    const float d = fmaf(X + B, X, C);
+    return fmaf(fmaf(X, sy, E), rcp_ftz(d), acc);
+}
+
+// Four-node value of a pair (valid for every r2 >= 64); *r2 = x^2 + y^2.
+__device__ __forceinline__ float gh4_val(float kf, float b, float nrb, float Y, float Ca,
+                                         float Cb, float sa, float sb, float *r2_out)
+{
+    const float x = fmaf(kf, b, nrb);
+    const float X = x * x;
+    const float r2 = X + Y;
+    const float da = fmaf(r2, r2, fmaf(-2.0f * kTa, X, Ca));
+    const float db = fmaf(r2, r2, fmaf(-2.0f * kTb, X, Cb));
+    *r2_out = r2;
+    return fmaf(sa * (r2 + kTa), db, sb * (r2 + kTb) * da) * rcp_ftz(da * db);
+}
+
+// Two lines' two-node values with one reciprocal, n0/d0 + n1/d1 =
+// (n0 d1 + n1 d0) / (d0 d1): the same issue count as two reciprocals and half
+// the MUFU work.  The caller bounds r2 (d <= (r2 + 1)^2) so that the products
+// stay in the float range.
+__device__ __forceinline__ float gh2_pair_acc(float kf0, float b0, float nrb0, float B0, float C0,
+                                              float sy0, float E0, float kf1, float b1, float nrb1,
+                                              float B1, float C1, float sy1, float E1, float acc)
+{
+    const float x0 = fmaf(kf0, b0, nrb0), x1 = fmaf(kf1, b1, nrb1);
+    const float X0 = x0 * x0, X1 = x1 * x1;
+    const float d0 = fmaf(X0 + B0, X0, C0), d1 = fmaf(X1 + B1, X1, C1);
+    const float n0 = fmaf(X0, sy0, E0), n1 = fmaf(X1, sy1, E1);
+    return fmaf(fmaf(n0, d1, n1 * d0), rcp_ftz(d0 * d1), acc);
+}
+
+// Largest r2 = x^2 + y^2 of lines (b, Y) at integer offsets |k| <= kmax from
+// their nearest bin (|rn| <= 1/2), as a bound for the shared reciprocals:
+// below kShareR2 both the denominators' product and the numerators' products
+// stay far inside the float range.
+constexpr float kShareR2 = 2.5e8f;
+__device__ __forceinline__ float r2_bound(float kmax, float b, float Y)
+{
+    const float xm = (kmax + 0.5f) * b;
+    return fmaf(xm, xm, Y);
+}
+
+template <int V>
+__device__ __forceinline__ void do_batch(Smem &S, int warp, int j0, int tg0, int tg1, float *base,
+                                         int lane, unsigned *queue, int &qn, int t0)
+{
+    const Rec *R = &S.rec[warp][j0];
+    const int c0 = R[0].c, gA = R[0].gA, gB = R[0].gB;
+    int mL4 = INT_MAX, MR4 = INT_MIN;
+    bool uni = gA <= gB;
+#pragma unroll
+    for (int j = 0; j < NLB; ++j) {
+        uni = uni && R[j].gA == gA && R[j].gB == gB && R[j].c == c0;
+        if (R[j].L4 <= R[j].R4) {
+            mL4 = min(mL4, R[j].L4);
+            MR4 = max(MR4, R[j].R4);
+        }
+    }
+    const bool central = mL4 <= MR4;
+    uni = uni && (!central || (mL4 > gA && MR4 < gB));
+    if (!uni) {   // warp-uniform
+        for (int j = 0; j < NLB; ++j) {
+            const Rec q = S.rec[warp][j0 + j];
+            do_line<V>(q, j0 + j, tg0, tg1, base, lane, queue, qn, S, warp, t0);
+        }
+        return;
+    }
+    if (max(gA, tg0) > min(gB, tg1)) return;
+    float b[NLB], nrb[NLB], B[NLB], C[NLB], sy[NLB], E[NLB];
+#pragma unroll
+    for (int j = 0; j < NLB; ++j) {
+        b[j] = R[j].b;
+        nrb[j] = -R[j].rnb;        // x = (k - rn) b, the per-line path's arithmetic
+        const float Y = R[j].Y, Yh = Y + 0.5f;
+        B[j] = fmaf(2.0f, Y, -1.0f);
+        C[j] = Yh * Yh;
+        sy[j] = R[j].sy;
+        E[j] = sy[j] * Yh;
+    }
+    const int kfc = lane - c0;
+    // every bin of the batch is within kmax bins of c0: pairs of lines share a
+    // reciprocal when their r2 stays below kShareR2
+    const float kmax = (float)max(c0 - 32 * gA, 32 * gB + 31 - c0);
+    bool share = true;
+#pragma unroll
+    for (int j = 0; j < NLB; ++j) share = share && r2_bound(kmax, b[j], R[j].Y) < kShareR2;
+    // the two-node rule over [g0, g1] (clipped to the tile), unmasked
+    auto interior = [&](int g0, int g1) {
+        g0 = max(g0, tg0);
+        g1 = min(g1, tg1);
+        if (g0 > g1) return;
+        float kf = (float)(32 * g0 + kfc);
+        float *p = base + 32 * (g0 - tg0);
+        float *const pe = base + 32 * (g1 - tg0);
+        if (share) {
+            for (; p <= pe; p += 32, kf += 32.0f) {
+                float v0 = 0.0f;
+#pragma unroll
+                for (int j = 0; j < NLB; j += 2)
+                    v0 = gh2_pair_acc(kf, b[j], nrb[j], B[j], C[j], sy[j], E[j], kf, b[j + 1],
+                                      nrb[j + 1], B[j + 1], C[j + 1], sy[j + 1], E[j + 1], v0);
+                p[0] += v0;
+            }
+        } else {
+            for (; p <= pe; p += 32, kf += 32.0f) {
+                float v0 = 0.0f;
+#pragma unroll
+                for (int j = 0; j < NLB; ++j)
+                    v0 = gh2_acc(kf, b[j], nrb[j], B[j], C[j], sy[j], E[j], v0);
+                p[0] += v0;
+            }
+        }
+    };
+    // an edge group: each line adds where its lane's bin is inside its range
+    auto edge = [&](int g) {
+        if (g < tg0 || g > tg1) return;
+        const float kf = (float)(32 * g + kfc);
+        float v = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NLB; ++j) {
+            const float t = gh2_acc(kf, b[j], nrb[j], B[j], C[j], sy[j], E[j], 0.0f);
+            const bool in = (unsigned)(32 * g + lane - R[j].lo) <= (unsigned)(R[j].hi - R[j].lo);
+            v += in ? t : 0.0f;
+        }
+        base[32 * (g - tg0)] += v;
+    };
+    edge(gA);
+    if (gB == gA) return;
+    edge(gB);
+    if (!central) {
+        interior(gA + 1, gB - 1);
+        return;
+    }
+    interior(gA + 1, mL4 - 1);
+    interior(MR4 + 1, gB - 1);
+    // the central groups: the four-node rule for every line (valid for every
+    // r2 >= 64), summed over two lines at a time; only inside a pair's core
+    // groups are a line's core bins (r2 < 64) told apart and queued.  The
+    // two-node parameters are dead here, which keeps the registers in bounds.
+    const int c0g = max(mL4, tg0), c1g = min(MR4, tg1);
+    if (c0g > c1g) return;
+    constexpr int NH = 2;
+#pragma unroll 1
+    for (int h = 0; h < NLB; h += NH) {
+        float bh[NH], nh[NH], Yh[NH], Ca[NH], Cb[NH], sa[NH], sb[NH];
+        int Lc[NH], Rc[NH];
+        int mLc = INT_MAX, MRc = INT_MIN;
+#pragma unroll
+        for (int j = 0; j < NH; ++j) {
+            const Rec &q = R[h + j];
+            bh[j] = q.b;
+            nh[j] = -q.rnb;
+            Yh[j] = q.Y;
+            Ca[j] = q.Ca;
+            Cb[j] = q.Cb;
+            sa[j] = q.sa;
+            sb[j] = q.sb;
+            Lc[j] = q.Lc;
+            Rc[j] = q.Rc;
+            if (Lc[j] <= Rc[j]) {
+                mLc = min(mLc, Lc[j]);
+                MRc = max(MRc, Rc[j]);
+            }
+        }
+        float kf = (float)(32 * c0g + kfc);
+        float *p = base + 32 * (c0g - tg0);
+        for (int g = c0g; g <= c1g; ++g, kf += 32.0f, p += 32) {
+            float v = 0.0f;
+            if (g < mLc || g > MRc) {   // no core bins here for either line (warp-uniform)
+#pragma unroll
+                for (int j = 0; j < NH; ++j) {
+                    float r2;
+                    v += gh4_val(kf, bh[j], nh[j], Yh[j], Ca[j], Cb[j], sa[j], sb[j], &r2);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NH; ++j) {
+                    float r2;
+                    const float t = gh4_val(kf, bh[j], nh[j], Yh[j], Ca[j], Cb[j], sa[j], sb[j], &r2);
+                    // core bins only inside the line's core groups (nested in its
+                    // band boundaries with a margin); elsewhere the four-node rule
+                    const bool cg = g >= Lc[j] && g <= Rc[j];   // warp-uniform
+                    const bool core = cg && r2 < 64.0f;
+                    v += core ? 0.0f : t;
+                    if (cg) {
+                        const unsigned m = __ballot_sync(0xffffffffu, core);
+                        if (m) {
+                            const int pos = qn + __popc(m & ((1u << lane) - 1u));
+                            if (core)
+                                queue[pos] = ((unsigned)(j0 + h + j) << 16) |
+                                             (unsigned)(32 * g + lane - t0);
+                            qn += __popc(m);
+                            __syncwarp();
+                            if (qn >= 32) {
+                                core_entry(S, warp, t0, queue[lane]);
+                                __syncwarp();
+                                if (lane < qn - 32) queue[lane] = queue[lane + 32];
+                                qn -= 32;
+                                __syncwarp();
+                            }
+                        }
+                    }
+                }
+            }
+            p[0] += v;
+        }
+    }
+}
+
+// Batches of wide lines (the peeled instances: Voigt and Lorentzian, with or
+// without the plinth).  The lines of a batch have their own centres, but a
+// tile far from all of them lies, for every line, inside one band clear of
+// the line's edge groups: then the warp sums the NLB lines per group in a
+// register (x from each line's exact integer bin offset, kept exact as a
+// float), one-node or two-node rule, less the lines' plinths.  Any other
+// (batch, tile) takes the per-line path.
+template <int V>
+__device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0, int tg1,
+                                              float *base, int lane, unsigned *queue, int &qn,
+                                              int t0)
+{
+    const Rec *R = &S.rec[warp][j0];
+    int cls = 0;   // 1: one-node rule over the whole tile for every line, 2: two-node
+#pragma unroll
+    for (int j = 0; j < NLB; ++j) {
+        const Rec &q = R[j];
+        int c = 0;
+        if (tg0 > q.gA && tg1 < q.gB) {
+            if (tg1 < q.L2 || tg0 > q.R2) c = 1;
+            else if (tg0 >= q.L2 && tg1 <= q.R2 && (tg1 < q.L4 || tg0 > q.R4)) c = 2;
+        }
+        cls = j == 0 ? c : (cls == c ? cls : 0);
+    }
+    if (cls == 0) {   // warp-uniform
+        for (int j = 0; j < NLB; ++j) {
+            const Rec q = S.rec[warp][j0 + j];
+            do_line<V>(q, j0 + j, tg0, tg1, base, lane, queue, qn, S, warp, t0);
+        }
+        return;
+    }
+    float kf[NLB], b[NLB], nrb[NLB], P1[NLB], P2[NLB], sy[NLB], P3[NLB];
+    float H = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NLB; ++j) {
+        kf[j] = (float)(32 * tg0 + lane - R[j].c);   // exact: |offset| < 2^24 bins
+        b[j] = R[j].b;
+        nrb[j] = -R[j].rnb;
+        sy[j] = R[j].sy;
+        const float Y = R[j].Y, Yh = Y + 0.5f;
+        P1[j] = cls == 1 ? Y : fmaf(2.0f, Y, -1.0f);
+        P2[j] = Yh * Yh;
+        P3[j] = sy[j] * Yh;
+        if (V & kVPlinth) H += R[j].h;
+    }
+    // pairs of lines share a reciprocal when every r2 of the tile stays below
+    // kShareR2 (one-node: 1/r2 products below 1e17^2 are safe as well)
+    bool share = true;
+#pragma unroll
+    for (int j = 0; j < NLB; ++j) {
+        const float km = (float)max(abs(32 * tg0 - R[j].c), abs(32 * tg1 + 31 - R[j].c));
+        share = share && r2_bound(km, b[j], R[j].Y) < (cls == 1 ? 1e17f : kShareR2);
+    }
+    float *p = base;
+    float *const pe = base + 32 * (tg1 - tg0);
+    if (cls == 1 && share) {
+        for (; p <= pe; p += 32) {
+            float v = -H;
+#pragma unroll
+            for (int j = 0; j < NLB; j += 2) {
+                const float x0 = fmaf(kf[j], b[j], nrb[j]), x1 = fmaf(kf[j + 1], b[j + 1], nrb[j + 1]);
+                const float r0 = fmaf(x0, x0, P1[j]), r1 = fmaf(x1, x1, P1[j + 1]);
+                v = fmaf(fmaf(sy[j], r1, sy[j + 1] * r0), rcp_ftz(r0 * r1), v);
+                kf[j] += 32.0f;
+                kf[j + 1] += 32.0f;
+            }
+            p[0] += v;
+        }
+    } else if (cls == 1) {
+        for (; p <= pe; p += 32) {
+            float v = -H;
+#pragma unroll
+            for (int j = 0; j < NLB; ++j) {
+                const float x = fmaf(kf[j], b[j], nrb[j]);
+                v = fmaf(sy[j], rcp_ftz(fmaf(x, x, P1[j])), v);
+                kf[j] += 32.0f;
+            }
+            p[0] += v;
+        }
+    } else if (share) {
+        for (; p <= pe; p += 32) {
+            float v = -H;
+#pragma unroll
+            for (int j = 0; j < NLB; j += 2) {
+                v = gh2_pair_acc(kf[j], b[j], nrb[j], P1[j], P2[j], sy[j], P3[j], kf[j + 1],
+                                 b[j + 1], nrb[j + 1], P1[j + 1], P2[j + 1], sy[j + 1], P3[j + 1], v);
+                kf[j] += 32.0f;
+                kf[j + 1] += 32.0f;
+            }
+            p[0] += v;
+        }
+    } else {
+        for (; p <= pe; p += 32) {
+            float v = -H;
+#pragma unroll
+            for (int j = 0; j < NLB; ++j) {
+                v = gh2_acc(kf[j], b[j], nrb[j], P1[j], P2[j], sy[j], P3[j], v);
+                kf[j] += 32.0f;
+            }
+            p[0] += v;
+        }
+    }
+}
+
 __device__ __forceinline__ void fold(Smem &S, int tid)
 {
     for (int i = tid; i < TILE; i += NT) {
@@ -493,12 +831,19 @@ __global__ void __launch_bounds__(NT, 3)
             S.rec[warp][lane] = q;
             __syncwarp();
             int qn = 0;
-            for (int j = 0; j < 32; ++j)
-            {
-                // a register copy: the record must not be re-read from shared
-                // memory after every store into the tile copy
-                const Rec q = S.rec[warp][j];
-                do_line<V>(q, j, tg0, tg1, accb, lane, queue, qn, S, warp, t0);
+            if (V == 0) {
+                for (int j0 = 0; j0 < 32; j0 += NLB)
+                    do_batch<V>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0);
+            } else if ((V & kVPeel) && !(V & (kVDoppler | kVBinned))) {
+                for (int j0 = 0; j0 < 32; j0 += NLB)
+                    do_batch_wide<V>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0);
+            } else {
+                for (int j = 0; j < 32; ++j) {
+                    // a register copy: the record must not be re-read from shared
+                    // memory after every store into the tile copy
+                    const Rec q = S.rec[warp][j];
+                    do_line<V>(q, j, tg0, tg1, accb, lane, queue, qn, S, warp, t0);
+                }
             }
             drain_rest(queue, qn, S, warp, lane, t0);
             if (++rounds == FLUSH_ROUNDS) {

@@ -50,6 +50,10 @@ int gather_profile(int mode, double *ms, int64_t *launches);
 int count_pairs_run(const Prob &p, const GridD &g, unsigned long long *counts_d, cudaStream_t st,
                     int num_sms);
 
+// Pipe-throughput microbenchmarks (hk_peaks.cu).  kind 0 FFMA, 1 MUFU
+// reciprocal, 2 MUFU exp2, 3 DFMA; scratch: >= num_sms * 8 * 256 doubles.
+int peak_launch(int kind, int iters, int num_sms, void *scratch, double *ops, cudaStream_t st);
+
 // Adjoint (hk_backward.cu).
 size_t backward_workspace(int64_t n, int nTP, int64_t nbins);
 int backward_run(Prob *probs_h, int nTP, const GridD &g, const float *grad_sigma,

@@ -30,7 +30,7 @@ EXPORTS = ["hk_line_strength", "hk_widths", "hk_voigt_accumulate", "hk_cross_sec
            "hk_autotune", "hk_sync_status", "hk_release", "hk_strerror", "hk_last_cuda_error",
            "hk_constants", "hk_version", "hk_count_pairs", "hk_profile",
            "hk_cross_section_noalloc", "hk_tuning", "hk_cross_section_host", "hk_set_tuning",
-           "hk_noalloc_status"]
+           "hk_noalloc_status", "hk_measure_peak"]
 
 
 class hk_lines(ctypes.Structure):
@@ -107,6 +107,7 @@ def lib():
     L.hk_cross_section_host.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts), vp,
                                         ctypes.c_int64, vp]
     L.hk_noalloc_status.argtypes = [vp]
+    L.hk_measure_peak.argtypes = [ctypes.c_int, ctypes.c_double, P(ctypes.c_double), vp]
     _lib = L
     return L
 
@@ -386,6 +387,18 @@ def hk_profile(mode: int):
     n = ctypes.c_int64(0)
     _check("hk_profile", lib().hk_profile(int(mode), ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, int(n.value)
+
+
+PEAK_FFMA, PEAK_RCP, PEAK_EX2, PEAK_DFMA = 0, 1, 2, 3
+
+
+def hk_measure_peak(kind: int, target_ms: float = 1000.0, stream=None) -> float:
+    """Measured operations per second of one pipe (instrumentation):
+    PEAK_FFMA (FMAs), PEAK_RCP, PEAK_EX2 (MUFU ops), PEAK_DFMA (FP64 FMAs)."""
+    v = ctypes.c_double(0.0)
+    _check("hk_measure_peak", lib().hk_measure_peak(int(kind), float(target_ms), ctypes.byref(v),
+                                                    _stream(stream)))
+    return float(v.value)
 
 
 def hk_tuning(precision: int = HK_FP32C) -> int:

@@ -598,3 +598,91 @@ def test_autotune_keeps_results(hk):
     after = hk.hk_cross_section(*args).cpu().numpy()
     hk.hk_sync_status()
     assert_sigma_close(after, before, "after autotune")
+
+
+def test_dense_line_batches(hk):
+    """Short lines (cut 25 at 0.1 cm^-1: 501 bins) in clusters that share a
+    nearest bin, so consecutive lines form batches with one group structure
+    (the multi-line sweep), mixed with clusters that straddle a half-bin (two
+    nearest bins in one batch: per-line path), lines so narrow in Doppler
+    width that no bin is in their four-node band, lines near the tile edges
+    (1024-bin tiles), and a ragged last cluster; FP32C against the oracle,
+    with the oracle's zero pattern."""
+    rng = np.random.default_rng(2101)
+    dnu, nbins = 0.1, 12000
+    centres = np.sort(rng.uniform(40.0, 1160.0, 420))
+    nu0 = []
+    for i, c in enumerate(centres):
+        k = int(round(c / dnu))
+        if i % 7 == 3:                       # a half-bin straddled inside the cluster
+            base = (k + 0.5) * dnu
+            offs = np.linspace(-3e-3, 3e-3, 9)
+        elif i % 11 == 5:                    # on a tile edge
+            base = (1024 * (1 + i % 10)) * dnu
+            offs = rng.uniform(-1e-3, 1e-3, 12)
+        else:                                # one shared nearest bin
+            base = k * dnu + rng.uniform(-0.04, 0.04)
+            offs = rng.uniform(-2e-3, 2e-3, int(rng.integers(4, 17)))
+        nu0.extend((base + np.sort(offs)).tolist())
+    nu0 = np.sort(np.asarray(nu0))
+    n = nu0.size
+    gam = rng.uniform(0.01, 0.1, n).astype(np.float32)
+    gam[rng.uniform(size=n) < 0.05] = 40.0   # y >> 50: no four-node band, all two-node
+    L = synth.LineList(nu0, (10 ** rng.uniform(-24, -20, n)).astype(np.float32),
+                       rng.exponential(1500.0, n).astype(np.float32), gam,
+                       rng.uniform(0.3, 0.8, n).astype(np.float32), 18.0)
+    grid = synth.Grid(0.0, dnu, nbins)
+    for T, P in [(1500.0, 1.0), (300.0, 0.05)]:
+        ref = oracle_sigma(L, grid, T, P, 25.0)
+        got = gpu_sigma(hk, L, grid, T, P, 25.0, 0, flags=hk.HK_SIGMA_F64)
+        assert_sigma_close(got, ref, f"dense batches T={T}")
+        assert np.array_equal(ref == 0, got == 0), T
+
+
+@pytest.mark.parametrize("cut", [1.5, 15.0])
+def test_voigt_bands_per_pair_accuracy(hk, cut):
+    """Per-pair accuracy of the FP32 Faddeeva evaluation, through
+    hk_voigt_accumulate: clusters of four identical lines (one batch), each
+    cluster alone on its bins, with alpha_D and y chosen so that the bins sweep
+    every band (the core r2 < 64 down to y = 1e-6, the four-, two- and
+    one-node bands out to r2 ~ 1e10); cut 1.5 takes the short-line instance,
+    cut 15 the wide-line one.  Every bin above 1e-15 of the peak against the
+    oracle's FP64 value on the same float inputs: FP32C at most 1e-5 relative
+    (the Gaussian tail inherits 2 x^2 times the relative rounding of x),
+    median below 1e-6; the FP64 GPU form (same bands) at most 3e-6.""" 
+    dnu = 0.01
+    spacing = 2.0 * cut + 1.0
+    params = [(y, a) for y in [1e-6, 1e-3, 0.05, 0.5, 2.0, 7.0, 40.0]
+              for a in [0.1, 0.02, 0.003, 1e-4]]
+    k = np.arange(len(params))
+    centre = spacing * (k + 1) + 0.00371 * k                  # off-bin centres
+    nu0 = np.repeat(centre, 4)
+    aDinv = np.repeat(np.array([1.0 / a for _, a in params], np.float32), 4)
+    yv = np.repeat(np.array([y for y, _ in params], np.float32), 4)
+    S = np.full(nu0.size, 1e-20)
+    aD = 1.0 / aDinv.astype(np.float64)                        # the kernel's inputs, exactly
+    GL = yv.astype(np.float64) * aD
+    nbins = int(round(spacing * (len(params) + 1) / dnu))
+    grid = synth.Grid(0.0, dnu, nbins)
+    ref = oracle.sigma(nu0, S, aD, GL, *grid.astuple(), cut)
+    out = torch.zeros(nbins, dtype=torch.float64, device="cuda")
+    hk.hk_voigt_accumulate(torch.from_numpy(nu0).cuda(), torch.from_numpy(S).cuda(),
+                           torch.from_numpy(aDinv).cuda(), torch.from_numpy(yv).cuda(),
+                           hk.make_grid(*grid.astuple()), cut, out, hk.HK_FP64)
+    hk.hk_sync_status()
+    out32 = torch.zeros(nbins, dtype=torch.float32, device="cuda")
+    hk.hk_voigt_accumulate(torch.from_numpy(nu0).cuda(), torch.from_numpy(S).cuda(),
+                           torch.from_numpy(aDinv).cuda(), torch.from_numpy(yv).cuda(),
+                           hk.make_grid(*grid.astuple()), cut, out32, hk.HK_FP32C)
+    hk.hk_sync_status()
+    m = ref > 1e-15 * ref.max()
+    # both GPU forms use the same truncated bands (~1e-6 by design); FP32C adds
+    # its rounding
+    for name, got, tol_max, tol_med in [("fp64", out.cpu().numpy(), 3e-6, 1e-6),
+                                        ("fp32c", out32.cpu().numpy().astype(np.float64), 1e-5,
+                                         1e-6)]:
+        rel = np.abs(got[m] - ref[m]) / ref[m]
+        i = int(np.argmax(rel))
+        assert rel.max() <= tol_max and np.median(rel) <= tol_med, (
+            name, cut, float(rel.max()), float(np.median(rel)), int(np.flatnonzero(m)[i]))
+    assert np.array_equal(ref == 0, out32.cpu().numpy() == 0)

@@ -58,7 +58,7 @@ def test_noalloc_limits(hk):
     st = hk.make_state(1000.0, 1.0, float(Q(1000.0)))
     op = hk.make_opts(QREF, 5.0)
     big = hk.make_grid(0.0, 1e-4, 3_000_000)         # FP32C needs ~24 MB > 16 MiB
-    out = torch.empty(8, dtype=torch.float32, device="cuda")
+    out = torch.empty(3_000_000, dtype=torch.float32, device="cuda")
     with pytest.raises(hk.HKError) as ei:
         hk.hk_cross_section_noalloc(D, big, st, op, out)
     assert ei.value.status == hk.HK_ESIZE
