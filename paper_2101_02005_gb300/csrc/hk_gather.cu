@@ -12,9 +12,10 @@
 //   the 152 SMs.
 // * Bin-parallel gather.  Each lane owns BPT bins of its warp's slice of the
 //   tile (lane-strided, so neighbouring lanes hold neighbouring bins and see
-//   the same Faddeeva band).  Lines are staged in shared memory in chunks of
-//   CHUNK; their parameters (bin geometry, S, widths) are computed once per
-//   chunk by one thread per line and read back as warp-wide broadcasts.
+//   the same Faddeeva band).  Each warp stages its own candidate lines (those
+//   within the cut of its bins, found by bisection on nu0), 32 at a time with
+//   one lane per line, and reads them back as warp-wide broadcasts: no warp
+//   waits for another inside an item.
 // * Accumulation.  FP32C: FP32 partial sums per lane, folded every FLUSH
 //   lines into a (hi, lo) two-sum pair; at the end of the item one FP64
 //   atomicAdd per bin into a per-problem FP64 accumulator (the final
@@ -36,7 +37,6 @@ namespace hk {
 
 constexpr int NWARPS = 8;
 constexpr int NTHREADS = NWARPS * 32;
-constexpr int CHUNK = NTHREADS;  // lines staged per pass: one prologue thread per line
 constexpr int FLUSH = 32;        // FP32 lines per two-sum fold
 
 template <typename R> struct LineT {
@@ -298,8 +298,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
              unsigned long long *counter)
 {
     constexpr int TILE = NWARPS * 32 * BPT;
-    __shared__ LineT<R> sl[CHUNK];
-    __shared__ double snu[CHUNK];
+    __shared__ LineT<R> sl[NWARPS * 32];   // 32 staged lines per warp
     __shared__ long long s_item, s_pt, s_lb, s_le;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -346,29 +345,32 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         for (int j = 0; j < BPT; ++j) acc[j] = shi[j] = slo[j] = R(0);
         int nsince = 0;
 
-        for (int64_t cs = l_begin; cs < l_end; cs += CHUNK) {
-            __syncthreads();
-            const int nl = (int)min((int64_t)CHUNK, l_end - cs);
-            if (tid < nl) stage_line<R>(pr, g, cs + tid, scale, &sl[tid], &snu[tid]);
-            __syncthreads();
-            // this warp's candidate lines inside the chunk (bisection on nu0)
-            int a = 0, b = nl;
-            if (has_cut(g)) {
-                int lo = 0, hi = nl;
-                while (lo < hi) {
-                    int m = (lo + hi) >> 1;
-                    if (snu[m] < wnu_lo) lo = m + 1; else hi = m;
-                }
-                a = lo;
-                hi = nl;
-                while (lo < hi) {
-                    int m = (lo + hi) >> 1;
-                    if (snu[m] <= wnu_hi) lo = m + 1; else hi = m;
-                }
-                b = lo;
+        // this warp's candidate lines among the item's (bisection on nu0); each
+        // warp stages its own lines, 32 at a time, so no warp waits for another
+        int64_t wa = l_begin, wb = l_end;
+        if (has_cut(g)) {
+            int64_t lo = l_begin, hi = l_end;
+            while (lo < hi) {
+                const int64_t m = (lo + hi) >> 1;
+                if (pr.nu0[m] < wnu_lo) lo = m + 1; else hi = m;
             }
-            for (int l = a; l < b; ++l) {
-                const LineT<R> q = sl[l];
+            wa = lo;
+            hi = l_end;
+            while (lo < hi) {
+                const int64_t m = (lo + hi) >> 1;
+                if (pr.nu0[m] <= wnu_hi) lo = m + 1; else hi = m;
+            }
+            wb = lo;
+        }
+        LineT<R> *const wsl = sl + warp * 32;
+        for (int64_t cs = wa; cs < wb; cs += 32) {
+            const int nl = (int)min((int64_t)32, wb - cs);
+            __syncwarp();
+            double nu_unused;
+            if (lane < nl) stage_line<R>(pr, g, cs + lane, scale, &wsl[lane], &nu_unused);
+            __syncwarp();
+            for (int l = 0; l < nl; ++l) {
+                const LineT<R> q = wsl[l];
                 if (q.hi < wb0 || q.lo > wb0 + 32 * BPT - 1) continue;  // warp-uniform
                 // x = (k - r) b for the integer bin offset k = bin - i0: formed as
                 // fma(k, b, -r b) with k exact, one rounding, so a bin next to the

@@ -51,15 +51,20 @@ constexpr int FLUSH_ROUNDS = 4;   // rounds (32 lines per warp each) between two
 // band segments are tile-independent group ranges.  Bands: gh1 (r2 >= 1.5e6),
 // gh2 (r2 >= 2500), gh4 (r2 >= 64), core (r2 < 64); a group takes the band
 // of its bin nearest the line centre.
+// The fields are grouped in 16-byte quads in the order a batch of lines reads
+// them (one 128-bit shared load per quad): two-node parameters, four-node
+// parameters, structure, ranges.
 struct __align__(16) Rec {
-    float b, rn, Y, s;          // x step per bin, centre offset from bin c, y^2, scaled strength
-    float rnb, sy, sy2, Yq;     // rn b, s y / sqrt(pi), sy / 2, Y + 1/4             (2 nodes)
+    float b, rnb, Y, sy;        // x step per bin, rn b, y^2, s y / sqrt(pi)
     float Ca, Cb, sa, sb;       // 2 tau Y + tau^2 for both 4-node pairs, 2 W sy      (4 nodes)
-    float y, h;                 // Gamma_L / alpha_D; the plinth s Re w(x_cut + iy) (or 0)
-    int c, lo, hi;              // nearest bin to the centre, inclusive bin range in the cut
-    int gA, gB, L2, R2;         // the line's groups; groups of band gh2 or inner
-    int L4, R4, Lc, Rc;         // groups of band gh4 or inner; groups holding core bins
+    int c, gA, gB, lo;          // nearest bin to the centre; the line's groups; first bin in the cut
+    int hi, L4, R4, cl;         // last bin; groups of band gh4 or inner; first core bin
+    int ch, Lc, Rc, L2;         // last core bin (core bins: r2 < 64); groups holding core bins;
+    int R2;                     //   groups of band gh2 or inner
+    float rn, s, y;             // centre offset from bin c, scaled strength, Gamma_L / alpha_D
+    float h, sy2, Yq, pad;      // the plinth s Re w(x_cut + iy) (or 0); sy / 2, Y + 1/4 (2 nodes)
 };
+static_assert(sizeof(Rec) == 112, "Rec is seven 16-byte quads");
 
 struct Smem {
     float acc[NW][TILE];
@@ -67,6 +72,7 @@ struct Smem {
     float lo[TILE];
     Rec rec[NW][32];
     unsigned queue[NW][QCAP];
+    float cval[NW][32];         // core values of one evaluation, by lane
 };
 
 // Bands of the non-Voigt profiles (the Lorentzian is the one-node band itself)
@@ -159,9 +165,25 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
     band_groups(1.5e6f, Y, b, q.rn, c, q.gA, q.gB, &q.L2, &q.R2);
     band_groups(2500.0f, Y, b, q.rn, c, q.L2, q.R2, &q.L4, &q.R4);
     band_groups(64.0f, Y, b, q.rn, c, q.L4, q.R4, &q.Lc, &q.Rc);
+    // the core bins themselves, c + k with |k - rn| < sqrt(64 - Y) / b, inside
+    // [lo, hi] (inside the core groups: those take a wider margin); empty: cl > ch
+    q.cl = 1;
+    q.ch = 0;
+    if (any && Y < 64.0f) {
+        const float Dc = fminf(sqrtf(64.0f - Y) / b, 1.0e9f);
+        const int kl = (int)floorf(q.rn - Dc) + 1, kh = (int)ceilf(q.rn + Dc) - 1;
+        const int a = max(c + kl, lo), e = min(c + kh, hi);
+        if (a <= e) {
+            q.cl = a;
+            q.ch = e;
+        }
+    }
+    q.pad = 0.0f;
     if (g.profile == kProfLorentz) {          // (y/sqrt(pi)) s / r2 on every bin: all one-node
         q.L2 = q.L4 = q.Lc = q.gB + 1;
         q.R2 = q.R4 = q.Rc = q.gB;
+        q.cl = 1;
+        q.ch = 0;
     }
     *out = q;
 }
@@ -310,13 +332,32 @@ __device__ __forceinline__ void sweep_binned(const Rec &q, int g0, int g1, int l
     }
 }
 
-__device__ __forceinline__ void core_entry(Smem &S, int warp, int t0, unsigned e)
+// Evaluates up to 32 queued core pairs, one per lane (lanes >= n idle), and
+// adds them into the warp's tile copy.  Entries may share a bin (the lines of
+// a batch share their centre): lanes of one bin, found by a match, add up
+// through the warp's scratch row and one of them updates the bin, so the
+// update needs no atomics.  Called by the whole warp.
+__device__ __forceinline__ void core_entry(Smem &S, int warp, int t0, unsigned e, int lane, int n)
 {
-    const Rec &qq = S.rec[warp][e >> 16];
-    const int tidx = (int)(e & 0xffffu);
-    const float kk = (float)(t0 + tidx - qq.c);
-    const float xx = fmaf(kk, qq.b, -qq.rnb);
-    atomicAdd(&S.acc[warp][tidx], qq.s * core_re<float>(xx, qq.y) - qq.h);
+    const bool valid = lane < n;
+    float v = 0.0f;
+    int tidx = -1 - lane;                        // distinct keys for idle lanes
+    if (valid) {
+        const Rec &qq = S.rec[warp][e >> 16];
+        tidx = (int)(e & 0xffffu);
+        const float kk = (float)(t0 + tidx - qq.c);
+        const float xx = fmaf(kk, qq.b, -qq.rnb);
+        v = qq.s * core_re<float>(xx, qq.y) - qq.h;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, tidx);
+    S.cval[warp][lane] = v;
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) {
+        float sum = v;
+        for (unsigned m = peers & (peers - 1u); m; m &= m - 1u) sum += S.cval[warp][__ffs(m) - 1];
+        S.acc[warp][tidx] += sum;
+    }
+    __syncwarp();
 }
 
 // Groups holding core bins: lanes with r2 >= 64 take the 4-node rule (valid
@@ -345,7 +386,7 @@ __device__ __forceinline__ void sweep_core(const Rec &q, int slot, int g0, int g
             qn += __popc(m);
             __syncwarp();
             if (qn >= 32) {
-                core_entry(S, warp, t0, queue[lane]);
+                core_entry(S, warp, t0, queue[lane], lane, 32);
                 __syncwarp();
                 if (lane < qn - 32) queue[lane] = queue[lane + 32];
                 qn -= 32;
@@ -359,7 +400,7 @@ __device__ __forceinline__ void drain_rest(unsigned *queue, int &qn, Smem &S, in
                                            int t0)
 {
     if (qn > 0) {
-        if (lane < qn) core_entry(S, warp, t0, queue[lane]);
+        core_entry(S, warp, t0, queue[lane], lane, qn);
         qn = 0;
     }
     __syncwarp();
@@ -482,20 +523,39 @@ __device__ __forceinline__ float r2_bound(float kmax, float b, float Y)
     return fmaf(xm, xm, Y);
 }
 
+// The i-th 16-byte quad of a record, as one 128-bit shared load.
+__device__ __forceinline__ float4 quadf(const Rec &q, int i)
+{
+    return reinterpret_cast<const float4 *>(&q)[i];
+}
+__device__ __forceinline__ int4 quadi(const Rec &q, int i)
+{
+    return reinterpret_cast<const int4 *>(&q)[i];
+}
+
+// Returns the lines (bit j for line j0 + j) whose core bins are left to the
+// caller's core-range pass: those of a batch that took the batched sweep.
 template <int V>
-__device__ __forceinline__ void do_batch(Smem &S, int warp, int j0, int tg0, int tg1, float *base,
-                                         int lane, unsigned *queue, int &qn, int t0)
+__device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0, int tg1,
+                                             float *base, int lane, unsigned *queue, int &qn,
+                                             int t0)
 {
     const Rec *R = &S.rec[warp][j0];
-    const int c0 = R[0].c, gA = R[0].gA, gB = R[0].gB;
+    int4 st[NLB], rg[NLB];     // (c, gA, gB, lo), (hi, L4, R4, cl)
+#pragma unroll
+    for (int j = 0; j < NLB; ++j) {
+        st[j] = quadi(R[j], 2);
+        rg[j] = quadi(R[j], 3);
+    }
+    const int c0 = st[0].x, gA = st[0].y, gB = st[0].z;
     int mL4 = INT_MAX, MR4 = INT_MIN;
     bool uni = gA <= gB;
 #pragma unroll
     for (int j = 0; j < NLB; ++j) {
-        uni = uni && R[j].gA == gA && R[j].gB == gB && R[j].c == c0;
-        if (R[j].L4 <= R[j].R4) {
-            mL4 = min(mL4, R[j].L4);
-            MR4 = max(MR4, R[j].R4);
+        uni = uni && st[j].y == gA && st[j].z == gB && st[j].x == c0;
+        if (rg[j].y <= rg[j].z) {
+            mL4 = min(mL4, rg[j].y);
+            MR4 = max(MR4, rg[j].z);
         }
     }
     const bool central = mL4 <= MR4;
@@ -505,27 +565,22 @@ __device__ __forceinline__ void do_batch(Smem &S, int warp, int j0, int tg0, int
             const Rec q = S.rec[warp][j0 + j];
             do_line<V>(q, j0 + j, tg0, tg1, base, lane, queue, qn, S, warp, t0);
         }
-        return;
+        return 0u;
     }
-    if (max(gA, tg0) > min(gB, tg1)) return;
+    if (max(gA, tg0) > min(gB, tg1)) return 0u;
     float b[NLB], nrb[NLB], B[NLB], C[NLB], sy[NLB], E[NLB];
 #pragma unroll
     for (int j = 0; j < NLB; ++j) {
-        b[j] = R[j].b;
-        nrb[j] = -R[j].rnb;        // x = (k - rn) b, the per-line path's arithmetic
-        const float Y = R[j].Y, Yh = Y + 0.5f;
-        B[j] = fmaf(2.0f, Y, -1.0f);
+        const float4 t = quadf(R[j], 0);   // (b, rn b, Y, sy)
+        b[j] = t.x;
+        nrb[j] = -t.y;              // x = (k - rn) b, the per-line path's arithmetic
+        const float Yh = t.z + 0.5f;
+        B[j] = fmaf(2.0f, t.z, -1.0f);
         C[j] = Yh * Yh;
-        sy[j] = R[j].sy;
-        E[j] = sy[j] * Yh;
+        sy[j] = t.w;
+        E[j] = t.w * Yh;
     }
     const int kfc = lane - c0;
-    // every bin of the batch is within kmax bins of c0: pairs of lines share a
-    // reciprocal when their r2 stays below kShareR2
-    const float kmax = (float)max(c0 - 32 * gA, 32 * gB + 31 - c0);
-    bool share = true;
-#pragma unroll
-    for (int j = 0; j < NLB; ++j) share = share && r2_bound(kmax, b[j], R[j].Y) < kShareR2;
     // the two-node rule over [g0, g1] (clipped to the tile), unmasked
     auto interior = [&](int g0, int g1) {
         g0 = max(g0, tg0);
@@ -534,119 +589,102 @@ __device__ __forceinline__ void do_batch(Smem &S, int warp, int j0, int tg0, int
         float kf = (float)(32 * g0 + kfc);
         float *p = base + 32 * (g0 - tg0);
         float *const pe = base + 32 * (g1 - tg0);
-        if (share) {
-            for (; p <= pe; p += 32, kf += 32.0f) {
-                float v0 = 0.0f;
+        for (; p <= pe; p += 32, kf += 32.0f) {
+            float v0 = 0.0f;
 #pragma unroll
-                for (int j = 0; j < NLB; j += 2)
-                    v0 = gh2_pair_acc(kf, b[j], nrb[j], B[j], C[j], sy[j], E[j], kf, b[j + 1],
-                                      nrb[j + 1], B[j + 1], C[j + 1], sy[j + 1], E[j + 1], v0);
-                p[0] += v0;
-            }
-        } else {
-            for (; p <= pe; p += 32, kf += 32.0f) {
-                float v0 = 0.0f;
-#pragma unroll
-                for (int j = 0; j < NLB; ++j)
-                    v0 = gh2_acc(kf, b[j], nrb[j], B[j], C[j], sy[j], E[j], v0);
-                p[0] += v0;
-            }
+            for (int j = 0; j < NLB; ++j)
+                v0 = gh2_acc(kf, b[j], nrb[j], B[j], C[j], sy[j], E[j], v0);
+            p[0] += v0;
         }
     };
     // an edge group: each line adds where its lane's bin is inside its range
     auto edge = [&](int g) {
         if (g < tg0 || g > tg1) return;
         const float kf = (float)(32 * g + kfc);
+        const int bin = 32 * g + lane;
         float v = 0.0f;
 #pragma unroll
         for (int j = 0; j < NLB; ++j) {
             const float t = gh2_acc(kf, b[j], nrb[j], B[j], C[j], sy[j], E[j], 0.0f);
-            const bool in = (unsigned)(32 * g + lane - R[j].lo) <= (unsigned)(R[j].hi - R[j].lo);
-            v += in ? t : 0.0f;
+            v += (bin >= R[j].lo && bin <= R[j].hi) ? t : 0.0f;
         }
         base[32 * (g - tg0)] += v;
     };
     edge(gA);
-    if (gB == gA) return;
+    if (gB == gA) return 0xfu;
     edge(gB);
     if (!central) {
         interior(gA + 1, gB - 1);
-        return;
+        return 0xfu;
     }
     interior(gA + 1, mL4 - 1);
     interior(MR4 + 1, gB - 1);
-    // the central groups: the four-node rule for every line (valid for every
-    // r2 >= 64), summed over two lines at a time; only inside a pair's core
-    // groups are a line's core bins (r2 < 64) told apart and queued.  The
-    // two-node parameters are dead here, which keeps the registers in bounds.
+    // the central groups: the four-node rule (valid for every r2 >= 64) for
+    // every bin but each line's core bins, summed over the batch; the core
+    // bins go to the caller's core-range pass.  The two-node parameters are
+    // dead here, which keeps the registers in bounds.
     const int c0g = max(mL4, tg0), c1g = min(MR4, tg1);
-    if (c0g > c1g) return;
-    constexpr int NH = 2;
-#pragma unroll 1
-    for (int h = 0; h < NLB; h += NH) {
-        float bh[NH], nh[NH], Yh[NH], Ca[NH], Cb[NH], sa[NH], sb[NH];
-        int Lc[NH], Rc[NH];
-        int mLc = INT_MAX, MRc = INT_MIN;
+    if (c0g > c1g) return 0xfu;
+    // (the four-node constants are read from shared memory in the loop: a
+    // 128-bit load per line and group costs less than holding them)
+    float kf = (float)(32 * c0g + kfc);
+    float *p = base + 32 * (c0g - tg0);
+    for (int g = c0g; g <= c1g; ++g, kf += 32.0f, p += 32) {
+        const int bin = 32 * g + lane;
+        float v = 0.0f;
 #pragma unroll
-        for (int j = 0; j < NH; ++j) {
-            const Rec &q = R[h + j];
-            bh[j] = q.b;
-            nh[j] = -q.rnb;
-            Yh[j] = q.Y;
-            Ca[j] = q.Ca;
-            Cb[j] = q.Cb;
-            sa[j] = q.sa;
-            sb[j] = q.sb;
-            Lc[j] = q.Lc;
-            Rc[j] = q.Rc;
-            if (Lc[j] <= Rc[j]) {
-                mLc = min(mLc, Lc[j]);
-                MRc = max(MRc, Rc[j]);
-            }
+        for (int j = 0; j < NLB; ++j) {
+            const float4 f = quadf(R[j], 1);   // (Ca, Cb, sa, sb)
+            const int cl = quadi(R[j], 3).w, ch = quadi(R[j], 4).x;
+            float r2;
+            const float t = gh4_val(kf, b[j], nrb[j], quadf(R[j], 0).z, f.x, f.y, f.z, f.w, &r2);
+            v += (bin >= cl && bin <= ch) ? 0.0f : t;
         }
-        float kf = (float)(32 * c0g + kfc);
-        float *p = base + 32 * (c0g - tg0);
-        for (int g = c0g; g <= c1g; ++g, kf += 32.0f, p += 32) {
-            float v = 0.0f;
-            if (g < mLc || g > MRc) {   // no core bins here for either line (warp-uniform)
-#pragma unroll
-                for (int j = 0; j < NH; ++j) {
-                    float r2;
-                    v += gh4_val(kf, bh[j], nh[j], Yh[j], Ca[j], Cb[j], sa[j], sb[j], &r2);
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < NH; ++j) {
-                    float r2;
-                    const float t = gh4_val(kf, bh[j], nh[j], Yh[j], Ca[j], Cb[j], sa[j], sb[j], &r2);
-                    // core bins only inside the line's core groups (nested in its
-                    // band boundaries with a margin); elsewhere the four-node rule
-                    const bool cg = g >= Lc[j] && g <= Rc[j];   // warp-uniform
-                    const bool core = cg && r2 < 64.0f;
-                    v += core ? 0.0f : t;
-                    if (cg) {
-                        const unsigned m = __ballot_sync(0xffffffffu, core);
-                        if (m) {
-                            const int pos = qn + __popc(m & ((1u << lane) - 1u));
-                            if (core)
-                                queue[pos] = ((unsigned)(j0 + h + j) << 16) |
-                                             (unsigned)(32 * g + lane - t0);
-                            qn += __popc(m);
-                            __syncwarp();
-                            if (qn >= 32) {
-                                core_entry(S, warp, t0, queue[lane]);
-                                __syncwarp();
-                                if (lane < qn - 32) queue[lane] = queue[lane + 32];
-                                qn -= 32;
-                                __syncwarp();
-                            }
-                        }
-                    }
-                }
-            }
-            p[0] += v;
-        }
+        p[0] += v;
     }
+    return 0xfu;
+}
+
+// The core bins (r2 < 64) of the lines in `mask`, one contiguous bin range per
+// line clipped to the tile [t0, t1]: the ranges are laid end to end by a scan
+// across the lanes and evaluated 32 pairs at a time, whatever line each pair
+// belongs to.  The warp's queue rows serve as scratch (the queue is empty).
+__device__ __forceinline__ void core_ranges(Smem &S, int warp, int lane, unsigned mask, int t0,
+                                            int t1)
+{
+    const Rec &q = S.rec[warp][lane];
+    const int a = max(q.cl, t0), e = min(q.ch, t1);
+    const int cnt = ((mask >> lane) & 1u) && a <= e ? e - a + 1 : 0;
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    if (total == 0) return;   // warp-uniform
+    int *pre = reinterpret_cast<int *>(S.queue[warp]);   // exclusive prefix, by line
+    int *first = pre + 32;                                // first core bin in the tile, by line
+    pre[lane] = inc - cnt;
+    first[lane] = a;
+    __syncwarp();
+    for (int base = 0; base < total; base += 32) {
+        const int p = base + lane;
+        unsigned ent = 0u;
+        if (p < total) {
+            // the last line whose prefix is <= p holds pair p (lines without
+            // core bins share their successor's prefix)
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+                const int m = (lo + hi + 1) >> 1;
+                if (pre[m] <= p) lo = m;
+                else hi = m - 1;
+            }
+            ent = ((unsigned)lo << 16) | (unsigned)(first[lo] + (p - pre[lo]) - t0);
+        }
+        core_entry(S, warp, t0, ent, lane, min(32, total - base));
+    }
+    __syncwarp();
 }
 
 // Batches of wide lines (the peeled instances: Voigt and Lorentzian, with or
@@ -832,8 +870,11 @@ __global__ void __launch_bounds__(NT, 3)
             __syncwarp();
             int qn = 0;
             if (V == 0) {
+                unsigned rmask = 0u;
                 for (int j0 = 0; j0 < 32; j0 += NLB)
-                    do_batch<V>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0);
+                    rmask |= do_batch<V>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0) << j0;
+                drain_rest(queue, qn, S, warp, lane, t0);
+                core_ranges(S, warp, lane, rmask, t0, t1);
             } else if ((V & kVPeel) && !(V & (kVDoppler | kVBinned))) {
                 for (int j0 = 0; j0 < 32; j0 += NLB)
                     do_batch_wide<V>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0);

@@ -176,38 +176,21 @@ template <typename R> __device__ __forceinline__ R core_re(R x, R y)
     // float: nodes |t| <= 4.5 (shifted: -4.25 .. 4.75); the dropped terms are below
     // 1e-8 of Re w for every r2 < 64 (|x - t| >= 1/8 by the lattice shift)
     constexpr int NMAX = sizeof(R) == 4 ? 9 : 11;
-    if (sizeof(R) == 4) {
-        // adjacent nodes share one reciprocal, w_a/d_a + w_b/d_b =
-        // (w_a d_b + w_b d_a) / (d_a d_b): half the MUFU work (1/64 <= d < 231,
-        // so the products stay in range); two partial sums halve the chain
-        const R axs = ax - off * R(0.5);
-        R s0 = R(0), s1 = R(0);
+    // nodes t = (n + off) / 2: x - t = (x - off / 2) - n / 2
+    const R axs = ax - off * R(0.5);
 #pragma unroll
-        for (int n = -NMAX; n < NMAX; n += 2) {
-            const R wa = sh ? R(w1[n + 11]) : R(w0[n + 11]);
-            const R wb = sh ? R(w1[n + 12]) : R(w0[n + 12]);
-            const R ea = axs - R(0.5 * n), eb = axs - R(0.5 * (n + 1));
-            const R da = ea * ea + Y, db = eb * eb + Y;
-            const R v = (wa * db + wb * da) * Math<R>::div_(R(1), da * db);
-            if (((n + NMAX) >> 1) & 1) s1 += v;
-            else s0 += v;
-        }
-        const R wl = sh ? R(w1[NMAX + 11]) : R(w0[NMAX + 11]);
-        const R el = axs - R(0.5 * NMAX);
-        s = (s0 + Math<R>::div_(wl, el * el + Y)) + s1;
-    } else {
-#pragma unroll
-        for (int n = -NMAX; n <= NMAX; ++n) {
-            R t = (R(n) + off) * R(0.5);
-            R wt = sh ? R(w1[n + 11]) : R(w0[n + 11]);
-            R d = ax - t;
-            s += Math<R>::div_(wt, d * d + Y);
-        }
+    for (int n = -NMAX; n <= NMAX; ++n) {
+        R wt = sh ? R(w1[n + 11]) : R(w0[n + 11]);
+        R d = axs - R(0.5 * n);
+        s += Math<R>::div_(wt, d * d + Y);
     }
     R re = R(0.5 * kInvPi) * y * s;       // (h / pi) y sum e^{-t^2} / ((x-t)^2 + y^2)
     if (y < R(2)) {
         // Re[ 2 e^{-z^2} / (1 -/+ e^{-2 pi i z / h}) ], h = 1/2: eta = 4 pi y, theta = 4 pi x
-        R em = Math<R>::expm1_(R(4 * kPI) * y);  // e^eta - 1
+        // e^eta - 1; in float E itself is what matters (den >= 2 E), so the
+        // hardware exponential less 1 serves
+        R em = sizeof(R) == 4 ? (R)(__expf((float)(R(4 * kPI) * y)) - 1.0f)
+                              : Math<R>::expm1_(R(4 * kPI) * y);
         R E = R(1) + em;
         R sn, cs;
         R s2, c2;
@@ -229,7 +212,15 @@ template <typename R> __device__ __forceinline__ R core_re(R x, R y)
         }
         R num = c2 * (R(1) - E * cs) - s2 * E * sn;
         R den = em * em + R(2) * E * (R(1) - cs);
-        re += R(2) * Math<R>::exp_(Y - ax * ax) * num / den;
+        if (sizeof(R) == 4) {
+            // cs <= 0 on either lattice, so den >= 2 E >= 2: a bare reciprocal;
+            // the hardware exponential's relative error, |arg| * 2^-24, stays
+            // below ~1e-6 wherever this term matters (it is below e^-10 of Re w
+            // when |arg| > 16)
+            re += R(2) * (R)__expf((float)(Y - ax * ax)) * num * (R)rcp_ftz((float)den);
+        } else {
+            re += R(2) * Math<R>::exp_(Y - ax * ax) * num / den;
+        }
     }
     return re;
 }
