@@ -372,7 +372,7 @@ def batched_measure(w, hk, synth, dev, steps, warmup, peaks):
     flops_step = sum(FLOPS_PER_PAIR[b] * n for b, n in bands.items())
     big = max(range(len(species)), key=lambda i: species[i].n)
     hk.hk_autotune(species[big], grid, states[len(states) // 2], opts)
-    lmax = hk.hk_tuning(hk.HK_FP32C)
+    lmax, tile_bins = hk.hk_tuning_full(hk.HK_FP32C)
     need = hk.hk_workspace_size(0, species, len(states), grid, opts)
     ws = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
     out = torch.empty((len(species), len(states), w.grid.nbins), dtype=torch.float64, device=dev)
@@ -414,6 +414,7 @@ def batched_measure(w, hk, synth, dev, steps, warmup, peaks):
             "config": {"workload": w.name, "species_lines": [s.n for s in species],
                        "points": len(states), "pairs_per_step": counts[0],
                        "band_pairs": bands, "lmax_autotuned": lmax,
+                       "tile_bins_autotuned": tile_bins,
                        "sigma_out": "f64", "call": "hk_cross_section_batched"}}
     del out, ws, species
     torch.cuda.empty_cache()
@@ -479,7 +480,7 @@ def main():
     t_tune = time.perf_counter()
     hk.hk_autotune(D, grid, state, opts)
     t_tune = time.perf_counter() - t_tune
-    lmax = hk.hk_tuning(hk.HK_FP32C)
+    lmax, tile_bins = hk.hk_tuning_full(hk.HK_FP32C)
 
     for _ in range(args.warmup):
         step()
@@ -574,17 +575,31 @@ def main():
         s64 = torch.empty(w.grid.nbins, dtype=torch.float64, device=dev)
         hk.hk_cross_section(D64, grid, state, o64, s64)
         torch.cuda.synchronize()
+        hk.hk_profile(1)
         g0 = torch.cuda.Event(enable_timing=True)
         g1 = torch.cuda.Event(enable_timing=True)
         g0.record(stream)
         hk.hk_cross_section(D64, grid, state, o64, s64)
         g1.record(stream)
         torch.cuda.synchronize()
+        g64_ms, _ = hk.hk_profile(0)
         f64ms = g0.elapsed_time(g1)
-        c64 = hk.hk_count_pairs(D64, grid, state, o64)[0]
+        c64 = hk.hk_count_pairs(D64, grid, state, o64)
+        flops64 = sum(FLOPS_PER_PAIR[b] * n for b, n in
+                      zip(["gh1", "gh2", "gh3", "gh4", "core"], c64[1:]))
+        achieved64 = flops64 / (g64_ms / 1e3) / 1e12
+        peak64 = 2.0 * peaks_m["dfma"]["ops_per_s"] / 1e12
         fp64 = {"value": D64.n / (f64ms / 1e3), "unit": "lines/s",
-                "voigt_evals_per_s": c64 / (f64ms / 1e3), "ms": f64ms,
-                "sample": "every 10th line of the list, one step"}
+                "voigt_evals_per_s": c64[0] / (f64ms / 1e3), "ms": f64ms,
+                "sample": "every 10th line of the list, one step; every line admits the same "
+                          "2 cut/dnu + 1 bins whatever the density, so the whole list takes "
+                          "10x as long (%.1f s)" % (10 * f64ms / 1e3),
+                "fp32c_speedup": (D64.n / (f64ms / 1e3)) and value / (D64.n / (f64ms / 1e3)),
+                "roofline": {"bound": "fp64", "kernel": "k_gather<double, 2>",
+                             "achieved": achieved64, "peak": peak64, "unit": "TFLOP/s",
+                             "frac": achieved64 / peak64, "gather_ms": g64_ms,
+                             "peak_basis": "measured FP64 FMA throughput (hk_measure_peak) x 2",
+                             "cost_model": "the FP32C gather's flops per pair and band"}}
         del D64, s64
 
     # the batched opacity table (config 3: 4 species x 200 (T, P) points in one
@@ -631,7 +646,8 @@ def main():
                            "l2": "inputs (24 B/line, %.1f GB) larger than L2" % (24 * L.n / 1e9),
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                            "band_pairs": bands, "generation_s": round(t_gen, 1),
-                           "lmax_autotuned": lmax, "autotune_s": round(t_tune, 2)},
+                           "lmax_autotuned": lmax, "tile_bins_autotuned": tile_bins,
+                           "autotune_s": round(t_tune, 2)},
                 "voigt_evals_per_s": world * pairs / (ms_step / 1e3),
                 # per hk_cross_section: descriptor upload, scale prepass, tile
                 # ranges, scan, gather, finalize (see the launch list profile)

@@ -318,24 +318,28 @@ int hk_workspace_size(int kind, const hk_lines *species, int nspecies, int nTP,
 
 /* The self-tuning of Sect. 2.4.4 (the paper re-tunes its thread counts
  * during a run), done once: times the Voigt sum of this problem for each
- * candidate number of lines per work item (1024, 2048, 4096, 16384 and
- * 65536; small items balance uneven line density, large ones amortise
- * per-item costs) and
- * caches the fastest for the current device and opts->precision; later
- * calls, batched ones included, use it.  Runs the problem eight times and
- * synchronises `stream`.  Allocates one nbins-sized buffer while it runs. */
+ * candidate setting and caches the fastest for the current device and
+ * opts->precision; later calls, batched ones included, use it.  Candidates:
+ * lines per work item 1024, 2048, 4096, 16384 and 65536 (small items balance
+ * uneven line density, large ones amortise per-item costs) and, for
+ * HK_FP32C, a tile width of 1024 or 2048 bins (3 or 2 blocks of 8 warps per
+ * SM; wide lines visit half as many 2048-bin tiles).  Runs the problem twice
+ * per candidate (a warm-up and a timed call) and synchronises `stream`.
+ * Allocates one nbins-sized buffer while it runs. */
 int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
                 const hk_opts *opts, void *stream);
 
-/* The lines-per-item setting in use for a precision (defaults 2048 for
- * HK_FP32C and 16384 for HK_FP64 until
- * hk_autotune has run on this device).  lmax: HOST int. */
-int hk_tuning(int precision, int *lmax);
+/* The setting in use for a precision on the current device: lines per work
+ * item (defaults 2048 for HK_FP32C and 16384 for HK_FP64 until hk_autotune
+ * has run) and the tile width in bins (HK_FP32C default 1024; HK_FP64 512).
+ * lmax, tile_bins: HOST ints (tile_bins may be NULL). */
+int hk_tuning(int precision, int *lmax, int *tile_bins);
 
-/* Sets the lines-per-item setting for a precision on the current device, e.g.
- * to reuse a value hk_autotune found in an earlier process (no paper
- * counterpart).  lmax: 32 .. 2^24, else HK_EINVAL. */
-int hk_set_tuning(int precision, int lmax);
+/* Sets the setting for a precision on the current device, e.g. to reuse what
+ * hk_autotune found in an earlier process (no paper counterpart).  lmax: 32
+ * .. 2^24; tile_bins: 0 keeps the current width, else 1024 or 2048 for
+ * HK_FP32C, 512 for HK_FP64; other values give HK_EINVAL. */
+int hk_set_tuning(int precision, int lmax, int tile_bins);
 
 /* Instrumentation (no counterpart in the paper).  Counts the (line, bin)
  * pairs the cut admits for this problem: counts[0] = total (the algorithmic

@@ -119,8 +119,8 @@ static int num_sms()
 
 // ---- tuning cache (hk_autotune) --------------------------------------------
 struct Tune {
-    int bpt = 4;
-    int lmax = 16384;
+    int bpt = 4;        // FP64: bins per thread; FP32C: tile width in bins
+    int lmax = 16384;   // lines per work item
 };
 static std::mutex g_tune_mu;
 static std::map<std::pair<int, int>, Tune> g_tune;  // (device, precision) -> tuning
@@ -133,8 +133,12 @@ static Tune get_tune(int precision)
     auto it = g_tune.find({dev, precision});
     if (it != g_tune.end()) return it->second;
     Tune t;
-    if (precision == HK_FP64) t.bpt = 2;
-    else t.lmax = 2048;   // what hk_autotune picks for the benchmark's line lists
+    if (precision == HK_FP64) {
+        t.bpt = 2;
+    } else {
+        t.bpt = 1024;
+        t.lmax = 2048;
+    }
     return t;
 }
 
@@ -222,6 +226,7 @@ static GridD make_grid(const hk_grid *g, const hk_opts *o)
     d.cut_factor = perline ? o->cut : 0.0;
     d.plinth = (o && (o->flags & HK_REMOVE_PLINTH)) ? 1 : 0;
     d.profile = o ? o->profile : HK_PROFILE_VOIGT;
+    d.halo = 0;
     return d;
 }
 
@@ -239,6 +244,7 @@ static GridD make_grid_cut(const hk_grid *g, double cut)
     d.cut_factor = 0.0;
     d.plinth = 0;
     d.profile = HK_PROFILE_VOIGT;
+    d.halo = 0;
     return d;
 }
 
@@ -558,7 +564,7 @@ int hk_voigt_accumulate(const double *nu0, const double *S, const float *alphaD_
     p.pre = 1;
     GridD g = make_grid_cut(grid, cut);
     Tune t = get_tune(precision);
-    size_t need = gather_workspace(1, g.nbins, precision, t.bpt);
+    size_t need = gather_workspace(1, g, precision, t.bpt);
     char *ws;
     if ((rc = pool_get(need, &ws))) return rc;
     unsigned *sw = status_word();
@@ -580,7 +586,7 @@ static int cross_section_impl(const hk_lines *lines, const hk_grid *grid, const 
         cudaError_t e = cudaMemsetAsync(sigma_out, 0, b, st);
         return e ? fail_cuda(e) : HK_OK;
     }
-    size_t need = gather_workspace(1, g.nbins, prec, bpt);
+    size_t need = gather_workspace(1, g, prec, bpt);
     size_t sort_need = 0, cub_b = 0;
     if (!lines->sorted) sort_need = al(sort_bytes(lines->n, &cub_b));
     char *ws;
@@ -688,7 +694,7 @@ int hk_cross_section_host(const hk_lines *lines, const hk_grid *grid, const hk_s
                           lines->g_up,  lines->gamma_self, lines->delta};
     Tune t = get_tune(prec);
     const GridD g = make_grid(grid, opts);
-    const size_t need_g = al(gather_workspace(1, nbins, prec, t.bpt));
+    const size_t need_g = al(gather_workspace(1, g, prec, t.bpt));
     size_t cub_b = 0;
     const size_t sort_need = lines->sorted ? 0 : al(sort_bytes(C, &cub_b));
     size_t buf = al((size_t)C * 8);
@@ -810,7 +816,7 @@ int hk_cross_section_noalloc(const hk_lines *lines, const hk_grid *grid, const h
     if (lines->n > 0 && !lines->sorted) return HK_ENOTSUP;
     const int prec = opts->precision;
     Tune t = get_tune(prec);
-    const size_t need = gather_workspace(1, grid->nbins, prec, t.bpt);
+    const size_t need = gather_workspace(1, make_grid(grid, opts), prec, t.bpt);
     if (need + 256 > (size_t)HK_NOALLOC_SCRATCH_BYTES) return HK_ESIZE;
     char *scratch;
     if ((rc = noalloc_scratch(&scratch))) return rc;
@@ -862,7 +868,7 @@ int hk_workspace_size(int kind, const hk_lines *species, int nspecies, int nTP,
     size_t total = 0;
     if (kind == 0) {
         Tune t = get_tune(opts->precision);
-        total = gather_workspace(nspecies * nTP, grid->nbins, HK_FP32C, t.bpt);
+        total = gather_workspace(nspecies * nTP, make_grid(grid, opts), HK_FP32C, t.bpt);
         for (int s = 0; s < nspecies; ++s) {
             if ((rc = check_lines(&species[s], true))) return rc;
             if (!species[s].sorted && species[s].n > 0) {
@@ -899,7 +905,7 @@ int hk_cross_section_batched(const hk_lines *species, int nspecies, const hk_sta
     if (!workspace || ws_bytes < need) return HK_ENOMEM;
     cudaStream_t st = (cudaStream_t)stream;
     Tune t = get_tune(HK_FP32C);
-    size_t gneed = gather_workspace(nspecies * nTP, grid->nbins, HK_FP32C, t.bpt);
+    size_t gneed = gather_workspace(nspecies * nTP, make_grid(grid, opts), HK_FP32C, t.bpt);
     char *sort_ws = (char *)workspace + gneed;
     std::vector<hk_lines> L(species, species + nspecies);
     for (int s = 0; s < nspecies; ++s) {
@@ -976,12 +982,15 @@ int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *stat
     if (lines->n == 0) return HK_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const int prec = opts->precision;
-    const int bpt = get_tune(prec).bpt;
     // lines per work item: small items balance uneven line density across the
     // SMs, large ones cut the per-item cost (record setup, one FP64 atomic per
-    // bin of the tile)
+    // bin of the tile); FP32C also the tile width: 1024 bins (3 blocks of 8
+    // warps per SM) or 2048 (2 blocks; half the tile visits of a wide line)
     const int lmaxs[] = {1024, 2048, 4096, 16384, 65536};
-    const int ncand = (int)(sizeof(lmaxs) / sizeof(lmaxs[0]));
+    const int nl = (int)(sizeof(lmaxs) / sizeof(lmaxs[0]));
+    const int tiles[] = {1024, 2048};
+    const int nt = prec == HK_FP32C ? 2 : 1;
+    const int ncand = nl * nt;
     size_t out_b = (size_t)grid->nbins * 8;
     // the output buffer lives in its own cudaMalloc (the pool is used by the runs)
     void *out = nullptr;
@@ -1003,13 +1012,15 @@ int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *stat
     Tune best = get_tune(prec);
     float best_ms = 1e30f;
     for (int j = 0; j < ncand && rc == HK_OK; ++j) {
-        rc = cross_section_impl(lines, grid, state, &o, out, st, bpt, lmaxs[j]);  // warm-up
+        const int bpt = prec == HK_FP32C ? tiles[j / nl] : get_tune(prec).bpt;
+        const int lmax = lmaxs[j % nl];
+        rc = cross_section_impl(lines, grid, state, &o, out, st, bpt, lmax);  // warm-up
         if (rc) break;
         if ((ce = cudaEventRecord(e0, st))) {
             rc = fail_cuda(ce);
             break;
         }
-        rc = cross_section_impl(lines, grid, state, &o, out, st, bpt, lmaxs[j]);
+        rc = cross_section_impl(lines, grid, state, &o, out, st, bpt, lmax);
         if (rc) break;
         float ms = 0;
         if ((ce = cudaEventRecord(e1, st)) || (ce = cudaEventSynchronize(e1)) ||
@@ -1020,7 +1031,7 @@ int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *stat
         if (ms < best_ms) {
             best_ms = ms;
             best.bpt = bpt;
-            best.lmax = lmaxs[j];
+            best.lmax = lmax;
         }
     }
     cudaEventDestroy(e0);
@@ -1080,22 +1091,28 @@ int hk_measure_peak(int kind, double target_ms, double *ops_per_s, void *stream)
     return HK_OK;
 }
 
-int hk_tuning(int precision, int *lmax)
+int hk_tuning(int precision, int *lmax, int *tile_bins)
 {
     if ((precision != HK_FP32C && precision != HK_FP64) || !lmax) return HK_EINVAL;
-    *lmax = get_tune(precision).lmax;
+    const Tune t = get_tune(precision);
+    *lmax = t.lmax;
+    if (tile_bins) *tile_bins = gather_tile_bins(precision, t.bpt);
     return HK_OK;
 }
 
-int hk_set_tuning(int precision, int lmax)
+int hk_set_tuning(int precision, int lmax, int tile_bins)
 {
     if ((precision != HK_FP32C && precision != HK_FP64) || lmax < 32 || lmax > (1 << 24))
+        return HK_EINVAL;
+    if (tile_bins != 0 && (precision == HK_FP64 ? tile_bins != gather_tile_bins(HK_FP64, 2)
+                                                : !gather_f32_tile_ok(tile_bins)))
         return HK_EINVAL;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e) return fail_cuda(e);
     Tune t = get_tune(precision);
     t.lmax = lmax;
+    if (tile_bins != 0 && precision == HK_FP32C) t.bpt = tile_bins;
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[{dev, precision}] = t;
     return HK_OK;

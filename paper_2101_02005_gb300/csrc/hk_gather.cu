@@ -180,7 +180,18 @@ __global__ void k_tile_ranges(const Prob *__restrict__ probs, int nprob, GridD g
     int64_t t = idx - (int64_t)p * ntiles;
     const Prob &pr = probs[p];
     int64_t lb = 0, le = pr.n;
-    if (has_cut(g)) {
+    if (g.halo > 0) {
+        // the lines whose nearest bin lies in the tile's central tile_bins - 2H
+        // bins (a line a hair past a boundary still fits the halo: H >= W + 2)
+        const double step = (double)(tile_bins - 2 * g.halo);
+        const double lo_nu = t == 0 ? g.nu_min - g.cut - 2.0 * g.dnu
+                                    : g.nu_min + ((double)t * step - 0.5) * g.dnu;
+        lb = lower_bound_nu(pr.nu0, pr.n, lo_nu);
+        if (t == ntiles - 1)
+            le = upper_bound_nu(pr.nu0, pr.n, g.nu_min + (double)g.nbins * g.dnu + g.cut + 2.0 * g.dnu);
+        else
+            le = lower_bound_nu(pr.nu0, pr.n, g.nu_min + ((double)(t + 1) * step - 0.5) * g.dnu);
+    } else if (has_cut(g)) {
         const double cut = (g.W > 0.0 && !pr.delta) ? g.cut : *pr.cutmax;
         double lo_nu = g.nu_min + (double)(t * tile_bins) * g.dnu - cut - 2.0 * g.dnu;
         double hi_nu = g.nu_min + (double)(t * tile_bins + tile_bins - 1) * g.dnu + cut + 2.0 * g.dnu;
@@ -304,26 +315,15 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     for (;;) {
-        if (tid == 0) {
-            unsigned long long it = atomicAdd(counter, 1ull);
-            long long item = (long long)it;
-            // item_off has m + 1 entries; the last one is the number of items
-            long long total = item_off[m];
-            if (item >= total) {
-                s_item = -1;
-            } else {
-                long long a = 0, b = m;  // largest pt with item_off[pt] <= item
-                while (b - a > 1) {
-                    long long c = (a + b) >> 1;
-                    if (item_off[c] <= item) a = c; else b = c;
-                }
-                long long chunk = item - item_off[a];
-                long long lb = tile_lb[a] + chunk * lmax;
-                long long le = min((long long)tile_le[a], lb + lmax);
+        if (warp == 0) {
+            long long pt_, lb_, le_;
+            const long long item =
+                fetch_item(counter, item_off, m, tile_lb, tile_le, lmax, lane, &pt_, &lb_, &le_);
+            if (lane == 0) {
                 s_item = item;
-                s_pt = a;
-                s_lb = lb;
-                s_le = le;
+                s_pt = pt_;
+                s_lb = lb_;
+                s_le = le_;
             }
         }
         __syncthreads();
@@ -594,14 +594,22 @@ int upload_doubles(double *dst, const double *src, int n, cudaStream_t st)
 
 int gather_tile_bins(int precision, int bpt)
 {
-    (void)bpt;
-    return precision == 1 ? NWARPS * 32 * 2 : gather_f32_tile_bins();
+    return precision == 1 ? NWARPS * 32 * 2 : bpt;
 }
 
-size_t gather_workspace(int nprob, int64_t nbins, int precision, int bpt)
+// Tiles of a launch: ceil(nbins / tb), or with a halo H ceil(nbins / (tb - 2 H)).
+static int64_t tile_count(int64_t nbins, int64_t tb, int halo)
 {
+    const int64_t step = tb - 2 * (int64_t)halo;
+    return (nbins + step - 1) / step;
+}
+
+size_t gather_workspace(int nprob, const GridD &g, int precision, int bpt)
+{
+    const int64_t nbins = g.nbins;
     int64_t tb = gather_tile_bins(precision, bpt);
-    int64_t ntiles = (nbins + tb - 1) / tb;
+    // the halo tiling (used unless a pressure shift rules it out) needs more tiles
+    int64_t ntiles = tile_count(nbins, tb, precision == 0 ? halo_bins(g, (int)tb) : 0);
     int64_t m = (int64_t)nprob * ntiles;
     size_t bytes = 0;
     auto add = [&](size_t b) { bytes += (b + 255) & ~(size_t)255; };
@@ -622,7 +630,16 @@ int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt,
                unsigned *status_d, cudaStream_t st, int num_sms)
 {
     int64_t tb = gather_tile_bins(precision, bpt);
-    int64_t ntiles = (g.nbins + tb - 1) / tb;
+    // FP32C short lines: tiles with a halo (every line summed in the one tile
+    // that holds its centre), unless a pressure shift moves the centres
+    GridD gh = g;
+    gh.halo = 0;
+    if (precision == 0) {
+        bool shifted = false;
+        for (int p = 0; p < nprob; ++p) shifted |= probs_h[p].delta != nullptr;
+        if (!shifted) gh.halo = halo_bins(g, (int)tb);
+    }
+    const int64_t ntiles = tile_count(g.nbins, tb, gh.halo);
     int64_t m = (int64_t)nprob * ntiles;
     char *cur = ws;
     auto take = [&](size_t b) {
@@ -677,7 +694,7 @@ int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt,
     }
     {
         int64_t blocks = (m + 255) / 256;
-        k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(probs_d, nprob, g, (int)tb, ntiles, lmax,
+        k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(probs_d, nprob, gh, (int)tb, ntiles, lmax,
                                                         tile_lb, tile_le, counts);
         if ((e = cudaGetLastError())) return fail_cuda(e);
         k_scan<<<1, 1024, 0, st>>>(counts, m, item_off);
@@ -687,8 +704,8 @@ int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt,
         dim3 grid(num_sms * 2);
         gather_profile_record(st, true);
         if (precision == 0) {
-            int rc = gather_f32_launch(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
-                                       counter, st, num_sms);
+            int rc = gather_f32_launch(probs_d, gh, ntiles, m, item_off, tile_lb, tile_le, lmax,
+                                       counter, st, num_sms, (int)tb);
             if (rc) return rc;
         } else {
             k_gather<double, 2><<<grid, NTHREADS, 0, st>>>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter);

@@ -41,7 +41,7 @@ namespace f32g {
 
 constexpr int NW = 8;             // warps per block
 constexpr int NT = NW * 32;
-constexpr int TILE = 1024;        // bins per tile
+constexpr int TILE_MAX = 2048;    // widest tile (bins); the tile width is a launch parameter
 constexpr int QCAP = 64;          // core-queue entries per warp
 constexpr int FLUSH_ROUNDS = 4;   // rounds (32 lines per warp each) between two-sum folds
 
@@ -66,14 +66,14 @@ struct __align__(16) Rec {
 };
 static_assert(sizeof(Rec) == 112, "Rec is seven 16-byte quads");
 
+// Shared memory: this fixed part, then the tile-sized arrays
+// float acc[NW][tile] (each warp's FP32 copy of the tile), hi[tile], lo[tile].
 struct Smem {
-    float acc[NW][TILE];
-    float hi[TILE];
-    float lo[TILE];
     Rec rec[NW][32];
     unsigned queue[NW][QCAP];
     float cval[NW][32];         // core values of one evaluation, by lane
 };
+static_assert(sizeof(Smem) % 16 == 0, "the tile arrays follow 16-byte aligned");
 
 // Bands of the non-Voigt profiles (the Lorentzian is the one-node band itself)
 constexpr int kBandGauss = 10, kBandBinned = 11;
@@ -337,7 +337,8 @@ __device__ __forceinline__ void sweep_binned(const Rec &q, int g0, int g1, int l
 // a batch share their centre): lanes of one bin, found by a match, add up
 // through the warp's scratch row and one of them updates the bin, so the
 // update needs no atomics.  Called by the whole warp.
-__device__ __forceinline__ void core_entry(Smem &S, int warp, int t0, unsigned e, int lane, int n)
+__device__ __forceinline__ void core_entry(Smem &S, int warp, int t0, unsigned e, int lane, int n,
+                                           float *accw)
 {
     const bool valid = lane < n;
     float v = 0.0f;
@@ -355,7 +356,7 @@ __device__ __forceinline__ void core_entry(Smem &S, int warp, int t0, unsigned e
     if (valid && lane == __ffs(peers) - 1) {
         float sum = v;
         for (unsigned m = peers & (peers - 1u); m; m &= m - 1u) sum += S.cval[warp][__ffs(m) - 1];
-        S.acc[warp][tidx] += sum;
+        accw[tidx] += sum;
     }
     __syncwarp();
 }
@@ -386,7 +387,7 @@ __device__ __forceinline__ void sweep_core(const Rec &q, int slot, int g0, int g
             qn += __popc(m);
             __syncwarp();
             if (qn >= 32) {
-                core_entry(S, warp, t0, queue[lane], lane, 32);
+                core_entry(S, warp, t0, queue[lane], lane, 32, base - lane);
                 __syncwarp();
                 if (lane < qn - 32) queue[lane] = queue[lane + 32];
                 qn -= 32;
@@ -397,10 +398,10 @@ __device__ __forceinline__ void sweep_core(const Rec &q, int slot, int g0, int g
 }
 
 __device__ __forceinline__ void drain_rest(unsigned *queue, int &qn, Smem &S, int warp, int lane,
-                                           int t0)
+                                           int t0, float *accw)
 {
     if (qn > 0) {
-        core_entry(S, warp, t0, queue[lane], lane, qn);
+        core_entry(S, warp, t0, queue[lane], lane, qn, accw);
         qn = 0;
     }
     __syncwarp();
@@ -645,44 +646,75 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
     return 0xfu;
 }
 
-// The core bins (r2 < 64) of the lines in `mask`, one contiguous bin range per
-// line clipped to the tile [t0, t1]: the ranges are laid end to end by a scan
-// across the lanes and evaluated 32 pairs at a time, whatever line each pair
-// belongs to.  The warp's queue rows serve as scratch (the queue is empty).
-__device__ __forceinline__ void core_ranges(Smem &S, int warp, int lane, unsigned mask, int t0,
-                                            int t1)
+// The core bins (r2 < 64) of the batches whose lines took the batched sweep
+// (`mask`: 4 bits per batch).  Each line's core bins are a contiguous range
+// (Rec::cl .. ch) and the 4 lines of a batch share their centre bin, so a
+// batch's core pairs lie in one short union range U of bins.  The pairs of
+// all such batches are laid end to end as (batch, bin u in U, line) with the
+// line innermost -- 4 slots per bin, so the lanes of an aligned quad hold one
+// bin's 4 values, summed by two shuffles and added by one lane -- and
+// evaluated 32 slots at a time.  A slot whose line has no core pair at u adds
+// 0.  Quads of two batches in one step may share a bin: the update is a
+// shared-memory atomic add.  The warp's queue rows serve as scratch (the
+// queue is empty here).
+__device__ __forceinline__ void core_quads(Smem &S, int warp, int lane, unsigned mask, int t0,
+                                           int t1, float *accw)
 {
-    const Rec &q = S.rec[warp][lane];
-    const int a = max(q.cl, t0), e = min(q.ch, t1);
-    const int cnt = ((mask >> lane) & 1u) && a <= e ? e - a + 1 : 0;
-    int inc = cnt;
+    int u0 = 0, nu = 0;
+    if (lane < 8 && ((mask >> (4 * lane)) & 0xfu) == 0xfu) {
+        int lo = INT_MAX, hi = INT_MIN;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
+        for (int j = 0; j < 4; ++j) {
+            const Rec &q = S.rec[warp][4 * lane + j];
+            const int cl = quadi(q, 3).w, ch = quadi(q, 4).x;
+            if (cl <= ch) {
+                lo = min(lo, cl);
+                hi = max(hi, ch);
+            }
+        }
+        lo = max(lo, t0);
+        hi = min(hi, t1);
+        if (lo <= hi) {
+            u0 = lo;
+            nu = hi - lo + 1;
+        }
+    }
+    int inc = 4 * nu;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += t;
     }
-    const int total = __shfl_sync(0xffffffffu, inc, 31);
+    const int total = __shfl_sync(0xffffffffu, inc, 7);
     if (total == 0) return;   // warp-uniform
-    int *pre = reinterpret_cast<int *>(S.queue[warp]);   // exclusive prefix, by line
-    int *first = pre + 32;                                // first core bin in the tile, by line
-    pre[lane] = inc - cnt;
-    first[lane] = a;
+    int *pre = reinterpret_cast<int *>(S.queue[warp]);   // first slot of batch k
+    int *ub = pre + 8;                                   // first bin of U of batch k
+    if (lane < 8) {
+        pre[lane] = inc - 4 * nu;
+        ub[lane] = u0;
+    }
     __syncwarp();
     for (int base = 0; base < total; base += 32) {
-        const int p = base + lane;
-        unsigned ent = 0u;
-        if (p < total) {
-            // the last line whose prefix is <= p holds pair p (lines without
-            // core bins share their successor's prefix)
-            int lo = 0, hi = 31;
-            while (lo < hi) {
-                const int m = (lo + hi + 1) >> 1;
-                if (pre[m] <= p) lo = m;
-                else hi = m - 1;
-            }
-            ent = ((unsigned)lo << 16) | (unsigned)(first[lo] + (p - pre[lo]) - t0);
+        const int sl = base + lane;
+        // the last batch whose first slot is <= sl (batches without core
+        // slots share their successor's first slot)
+        int k = 0;
+#pragma unroll
+        for (int st = 4; st > 0; st >>= 1)
+            if (k + st < 8 && pre[k + st] <= sl) k += st;
+        const int rel = sl - pre[k];
+        const int u = ub[k] + (rel >> 2);
+        const Rec &q = S.rec[warp][4 * k + (rel & 3)];
+        float v = 0.0f;
+        if (sl < total && u >= quadi(q, 3).w && u <= quadi(q, 4).x) {
+            const float4 p0 = quadf(q, 0);   // (b, rn b, Y, sy)
+            const float4 p5 = quadf(q, 5);   // (R2, rn, s, y)
+            const float kk = (float)(u - quadi(q, 2).x);
+            v = p5.z * core_re<float>(fmaf(kk, p0.x, -p0.y), p5.w) - q.h;
         }
-        core_entry(S, warp, t0, ent, lane, min(32, total - base));
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        if ((lane & 3) == 0 && sl < total && v != 0.0f) atomicAdd(&accw[u - t0], v);
     }
     __syncwarp();
 }
@@ -791,19 +823,19 @@ __device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0
     }
 }
 
-__device__ __forceinline__ void fold(Smem &S, int tid)
+__device__ __forceinline__ void fold(float *accs, float *hi, float *lo, int tile, int tid)
 {
-    for (int i = tid; i < TILE; i += NT) {
+    for (int i = tid; i < tile; i += NT) {
         float sum = 0.0f;
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
-            sum += S.acc[w][i];
-            S.acc[w][i] = 0.0f;
+            sum += accs[w * tile + i];
+            accs[w * tile + i] = 0.0f;
         }
         float h, e;
-        two_sum(S.hi[i], sum, &h, &e);
-        S.hi[i] = h;
-        S.lo[i] += e;
+        two_sum(hi[i], sum, &h, &e);
+        hi[i] = h;
+        lo[i] += e;
     }
 }
 
@@ -811,49 +843,48 @@ template <int V>
 __global__ void __launch_bounds__(NT, 3)
     k_gather_f32(const Prob *__restrict__ probs, GridD g, int64_t ntiles, int64_t m,
                  const int64_t *__restrict__ item_off, const int64_t *__restrict__ tile_lb,
-                 const int64_t *__restrict__ tile_le, int lmax, unsigned long long *counter)
+                 const int64_t *__restrict__ tile_le, int lmax, unsigned long long *counter,
+                 int tile)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem &S = *reinterpret_cast<Smem *>(smem_raw);
+    float *const accs = reinterpret_cast<float *>(smem_raw + sizeof(Smem));   // [NW][tile]
+    float *const shi = accs + NW * tile, *const slo = shi + tile;
     __shared__ long long s_item, s_pt, s_lb, s_le;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned *queue = S.queue[warp];
 
-    for (int i = tid; i < NW * TILE; i += NT) (&S.acc[0][0])[i] = 0.0f;
+    for (int i = tid; i < NW * tile; i += NT) accs[i] = 0.0f;
     for (;;) {
-        if (tid == 0) {
-            long long item = (long long)atomicAdd(counter, 1ull);
-            long long total = item_off[m];
-            if (item >= total) {
-                s_item = -1;
-            } else {
-                long long a = 0, b = m;
-                while (b - a > 1) {
-                    long long c = (a + b) >> 1;
-                    if (item_off[c] <= item) a = c; else b = c;
-                }
-                long long lb = tile_lb[a] + (item - item_off[a]) * lmax;
+        if (warp == 0) {
+            long long pt_, lb_, le_;
+            const long long item =
+                fetch_item(counter, item_off, m, tile_lb, tile_le, lmax, lane, &pt_, &lb_, &le_);
+            if (lane == 0) {
                 s_item = item;
-                s_pt = a;
-                s_lb = lb;
-                s_le = min((long long)tile_le[a], lb + lmax);
+                s_pt = pt_;
+                s_lb = lb_;
+                s_le = le_;
             }
         }
-        for (int i = tid; i < TILE; i += NT) {
-            S.hi[i] = 0.0f;
-            S.lo[i] = 0.0f;
+        for (int i = tid; i < tile; i += NT) {
+            shi[i] = 0.0f;
+            slo[i] = 0.0f;
         }
         __syncthreads();
         if (s_item < 0) break;
         const int64_t pt = s_pt;
         const int p = (int)(pt / ntiles);
-        const int t0 = (int)((pt - (int64_t)p * ntiles) * TILE);
-        const int t1 = (int)min((int64_t)t0 + TILE, g.nbins) - 1;  // last bin of the tile
+        // the tile's first bin; with a halo the window starts H bins before the
+        // central bins the tile owns (possibly before bin 0: those bins stay empty)
+        const int64_t tix = pt - (int64_t)p * ntiles;
+        const int t0 = g.halo ? (int)(tix * (tile - 2 * g.halo)) - g.halo : (int)(tix * tile);
+        const int t1 = (int)min((int64_t)t0 + tile, g.nbins) - 1;  // last bin of the tile
         const int64_t l_begin = s_lb, l_end = s_le;
         const Prob &pr = probs[p];
         const int scale = *pr.scale_exp;
         const int tg0 = t0 >> 5, tg1 = t1 >> 5;           // the tile's groups
-        float *accb = &S.acc[warp][0] + lane;
+        float *accb = accs + warp * tile + lane;
         int rounds = 0;
         for (int64_t base = l_begin; base < l_end; base += NT) {
             const int64_t l = base + tid;  // warp w owns lines base + 32 w + lane
@@ -873,8 +904,8 @@ __global__ void __launch_bounds__(NT, 3)
                 unsigned rmask = 0u;
                 for (int j0 = 0; j0 < 32; j0 += NLB)
                     rmask |= do_batch<V>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0) << j0;
-                drain_rest(queue, qn, S, warp, lane, t0);
-                core_ranges(S, warp, lane, rmask, t0, t1);
+                drain_rest(queue, qn, S, warp, lane, t0, accb - lane);
+                core_quads(S, warp, lane, rmask, t0, t1, accb - lane);
             } else if ((V & kVPeel) && !(V & (kVDoppler | kVBinned))) {
                 for (int j0 = 0; j0 < 32; j0 += NLB)
                     do_batch_wide<V>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0);
@@ -886,20 +917,20 @@ __global__ void __launch_bounds__(NT, 3)
                     do_line<V>(q, j, tg0, tg1, accb, lane, queue, qn, S, warp, t0);
                 }
             }
-            drain_rest(queue, qn, S, warp, lane, t0);
+            drain_rest(queue, qn, S, warp, lane, t0, accb - lane);
             if (++rounds == FLUSH_ROUNDS) {
                 rounds = 0;
                 __syncthreads();
-                fold(S, tid);
+                fold(accs, shi, slo, tile, tid);
                 __syncthreads();
             }
         }
         __syncthreads();
-        fold(S, tid);
+        fold(accs, shi, slo, tile, tid);
         __syncthreads();
         for (int i = tid; i <= t1 - t0; i += NT) {
-            const double tot = (double)S.hi[i] + (double)S.lo[i];
-            if (tot != 0.0) atomicAdd(pr.acc + t0 + i, tot);
+            const double tot = (double)shi[i] + (double)slo[i];
+            if (tot != 0.0 && t0 + i >= 0) atomicAdd(pr.acc + t0 + i, tot);
         }
         __syncthreads();
     }
@@ -907,37 +938,44 @@ __global__ void __launch_bounds__(NT, 3)
 
 }  // namespace f32g
 
-int gather_f32_tile_bins() { return f32g::TILE; }
+// Dynamic shared memory of a launch with `tile`-bin tiles.
+static size_t f32_smem(int tile) { return sizeof(f32g::Smem) + (size_t)(f32g::NW + 2) * tile * 4; }
 
-size_t gather_f32_smem() { return sizeof(f32g::Smem); }
+bool gather_f32_tile_ok(int tile) { return tile == 1024 || tile == 2048; }
 
 // Lines at least this many bins wide take the peeled sweeps.
 constexpr double kPeelBins = 1024.0;
 
-// Blocks per SM of a kernel instance on the current device, after raising its
-// dynamic shared-memory limit there (a per-device attribute): done once per
-// (device, instance) under a lock, so concurrent first calls from several host
+// Blocks per SM of a kernel instance on the current device for a dynamic
+// shared-memory size, after raising the instance's shared-memory limit there
+// to the widest tile's need (a per-device attribute): done once per (device,
+// instance, size) under a lock, so concurrent first calls from several host
 // threads, or a second device, each see a configured kernel.
 static int configure_once(const void *fn, size_t smem, int threads, int *per_sm_out)
 {
     static std::mutex mu;
-    static std::map<std::pair<int, const void *>, int> done;
+    static std::map<std::pair<int, const void *>, bool> limit_set;
+    static std::map<std::pair<std::pair<int, const void *>, size_t>, int> done;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e) return fail_cuda(e);
     std::lock_guard<std::mutex> lk(mu);
-    auto it = done.find({dev, fn});
+    auto it = done.find({{dev, fn}, smem});
     if (it != done.end()) {
         *per_sm_out = it->second;
         return HK_OK;
     }
-    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e) return fail_cuda(e);
+    if (!limit_set[{dev, fn}]) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)f32_smem(f32g::TILE_MAX));
+        if (e) return fail_cuda(e);
+        limit_set[{dev, fn}] = true;
+    }
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
     if (e) return fail_cuda(e);
     if (per_sm < 1) per_sm = 1;
-    done[{dev, fn}] = per_sm;
+    done[{{dev, fn}, smem}] = per_sm;
     *per_sm_out = per_sm;
     return HK_OK;
 }
@@ -946,23 +984,25 @@ template <int V>
 static int launch_variant(const Prob *probs_d, const GridD &g, int64_t ntiles, int64_t m,
                           const int64_t *item_off, const int64_t *tile_lb,
                           const int64_t *tile_le, int lmax, unsigned long long *counter,
-                          cudaStream_t st, int num_sms)
+                          cudaStream_t st, int num_sms, int tile)
 {
+    const size_t smem = f32_smem(tile);
     int per_sm = 0;
-    int rc = configure_once((const void *)f32g::k_gather_f32<V>, sizeof(f32g::Smem), f32g::NT,
-                            &per_sm);
+    int rc = configure_once((const void *)f32g::k_gather_f32<V>, smem, f32g::NT, &per_sm);
     if (rc) return rc;
     cudaError_t e;
-    f32g::k_gather_f32<V><<<num_sms * per_sm, f32g::NT, sizeof(f32g::Smem), st>>>(
-        probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter);
+    f32g::k_gather_f32<V><<<num_sms * per_sm, f32g::NT, smem, st>>>(
+        probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter, tile);
     e = cudaGetLastError();
     return e ? fail_cuda(e) : HK_OK;
 }
 
 int gather_f32_launch(const Prob *probs_d, const GridD &g, int64_t ntiles, int64_t m,
                       const int64_t *item_off, const int64_t *tile_lb, const int64_t *tile_le,
-                      int lmax, unsigned long long *counter, cudaStream_t st, int num_sms)
+                      int lmax, unsigned long long *counter, cudaStream_t st, int num_sms,
+                      int tile)
 {
+    if (!gather_f32_tile_ok(tile)) return HK_EINVAL;
     const bool wide = g.W <= 0.0 || 2.0 * g.W + 1.0 >= kPeelBins;
     // the Lorentzian is the one-node rule itself: it needs the one-node passes
     // that only the peeled instance keeps
@@ -973,22 +1013,22 @@ int gather_f32_launch(const Prob *probs_d, const GridD &g, int64_t ntiles, int64
     switch (v) {
     case f32g::kVPeel | f32g::kVPlinth | f32g::kVDoppler:
         return launch_variant<f32g::kVPeel | f32g::kVPlinth | f32g::kVDoppler>(
-            probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter, st, num_sms);
+            probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter, st, num_sms, tile);
     case f32g::kVPeel | f32g::kVPlinth | f32g::kVBinned:
         return launch_variant<f32g::kVPeel | f32g::kVPlinth | f32g::kVBinned>(
-            probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter, st, num_sms);
+            probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax, counter, st, num_sms, tile);
     case 0:
         return launch_variant<0>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
-                                 counter, st, num_sms);
+                                 counter, st, num_sms, tile);
     case 1:
         return launch_variant<1>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
-                                 counter, st, num_sms);
+                                 counter, st, num_sms, tile);
     case 2:
         return launch_variant<2>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
-                                 counter, st, num_sms);
+                                 counter, st, num_sms, tile);
     default:
         return launch_variant<3>(probs_d, g, ntiles, m, item_off, tile_lb, tile_le, lmax,
-                                 counter, st, num_sms);
+                                 counter, st, num_sms, tile);
     }
 }
 

@@ -323,7 +323,24 @@ struct GridD {
     double cut_factor;
     int plinth;                 // subtract each line's value at its cutting length
     int profile;                // kProf*
+    int halo;                   // FP32C short lines: tile halo in bins (0: tiles without halo)
 };
+
+// Tiles with a halo (FP32C, the short-line batch instance: Voigt profile,
+// fixed cut of 2W + 1 < 1024 bins, no plinth): a tile of `tile_bins` bins owns
+// the lines whose nearest bin lies in its central tile_bins - 2H bins, and
+// its window reaches H bins further on each side, H a multiple of 32 with
+// H >= W + 2 -- every line is summed in one tile, unclipped.  Returns H, or 0
+// when the cut is too wide to leave at least 256 central bins.
+__device__ __host__ __forceinline__ int halo_bins(const GridD &g, int tile_bins)
+{
+    if (g.cut_mode != kCutFixed || !(g.W > 0.0) || g.plinth || g.profile != kProfVoigt ||
+        2.0 * g.W + 1.0 >= 1024.0)
+        return 0;
+    const int need = (int)g.W + 3;   // ceil(W) + 2, W not an integer or W + 1 + 2
+    const int H = 32 * ((need + 31) / 32);
+    return tile_bins - 2 * H >= 256 ? H : 0;
+}
 
 // Whether the lines have a cut at all (fixed or per line).
 __device__ __host__ __forceinline__ bool has_cut(const GridD &g)
@@ -643,6 +660,41 @@ __device__ __forceinline__ void line_strength_f64(const Prob &p, int64_t l, doub
     *S_out = S * p.mass_scale;
     *aDinv_out = aDinv;
     *y_out = GL * aDinv;
+}
+
+// The work item of a persistent gather: called by a whole warp.  Lane 0 takes
+// the next item number from `counter`; the warp finds its (problem, tile)
+// entry -- the largest a with item_off[a] <= item in the non-decreasing
+// exclusive scan item_off[0..m] -- by a 32-way search (32 probes and a ballot
+// per step, so ~log32(m) dependent loads instead of log2(m)).  Returns the
+// item number (-1 once all are taken) and sets *pt, *lb, *le for it.
+__device__ __forceinline__ long long fetch_item(unsigned long long *counter,
+                                                const int64_t *__restrict__ item_off, int64_t m,
+                                                const int64_t *__restrict__ tile_lb,
+                                                const int64_t *__restrict__ tile_le, int lmax,
+                                                int lane, long long *pt, long long *lb,
+                                                long long *le)
+{
+    long long item = 0;
+    if (lane == 0) item = (long long)atomicAdd(counter, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    const long long total = item_off[m];
+    if (item >= total) return -1;
+    long long a = 0, b = m;   // item_off[a] <= item < item_off[b]
+    while (b - a > 1) {
+        const long long step = (b - a + 31) >> 5;
+        const long long idx = a + (long long)lane * step;
+        const bool le_ = idx < b && item_off[idx] <= item;
+        const unsigned msk = __ballot_sync(0xffffffffu, le_);   // a prefix of the lanes
+        const int k = 31 - __clz(msk);                           // lane 0 always holds
+        a += (long long)k * step;
+        b = min(b, a + step);
+    }
+    const long long l0 = tile_lb[a] + (item - item_off[a]) * lmax;
+    *pt = a;
+    *lb = l0;
+    *le = min((long long)tile_le[a], l0 + lmax);
+    return item;
 }
 
 // Two-sum: s + e = a + b exactly (Knuth).

@@ -19,10 +19,11 @@ int fail_cuda(cudaError_t e);
 int upload_probs(Prob *dst, const Prob *src, int n, cudaStream_t st);
 int upload_doubles(double *dst, const double *src, int n, cudaStream_t st);
 
-// Gather (hk_gather.cu).  Tile width in bins for a precision / bins-per-thread.
+// Gather (hk_gather.cu).  Tile width in bins: FP64, 512 (bpt 2 bins per
+// thread); FP32C, `bpt` itself is the tile width (1024 or 2048).
 int gather_tile_bins(int precision, int bpt);
 // Workspace bytes of gather_run for nprob sigma arrays of nbins bins.
-size_t gather_workspace(int nprob, int64_t nbins, int precision, int bpt);
+size_t gather_workspace(int nprob, const GridD &g, int precision, int bpt);
 // Runs the Voigt sum for nprob problems.  precision 0: FP32C, out is
 // float[nprob][nbins]; precision 1: FP64, out is double[nprob][nbins].
 // accumulate: add into out instead of overwriting.  probs_h is modified
@@ -36,12 +37,13 @@ int gather_run(Prob *probs_h, int nprob, const GridD &g, int precision, int bpt,
 // The per-device status word (allocated on first use).  Returns nullptr on failure.
 unsigned *status_word();
 
-// FP32-compensated line-major gather (hk_gather_f32.cu).
-int gather_f32_tile_bins();
-size_t gather_f32_smem();
+// FP32-compensated line-major gather (hk_gather_f32.cu).  tile: bins per
+// tile, one of the widths gather_f32_tile_ok accepts (1024, 2048).
+bool gather_f32_tile_ok(int tile);
 int gather_f32_launch(const Prob *probs_d, const GridD &g, int64_t ntiles, int64_t m,
                       const int64_t *item_off, const int64_t *tile_lb, const int64_t *tile_le,
-                      int lmax, unsigned long long *counter, cudaStream_t st, int num_sms);
+                      int lmax, unsigned long long *counter, cudaStream_t st, int num_sms,
+                      int tile);
 
 // Profiling of the gather launches (hk_profile).
 void gather_profile_record(cudaStream_t st, bool begin);

@@ -100,8 +100,8 @@ def lib():
     L.hk_count_pairs.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts),
                                  P(ctypes.c_int64), vp]
     L.hk_profile.argtypes = [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int64)]
-    L.hk_tuning.argtypes = [ctypes.c_int, P(ctypes.c_int)]
-    L.hk_set_tuning.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.hk_tuning.argtypes = [ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)]
+    L.hk_set_tuning.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.hk_cross_section_noalloc.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts),
                                            vp, vp]
     L.hk_cross_section_host.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts), vp,
@@ -403,14 +403,21 @@ def hk_measure_peak(kind: int, target_ms: float = 1000.0, stream=None) -> float:
 
 def hk_tuning(precision: int = HK_FP32C) -> int:
     """Lines per work item currently used for `precision`."""
+    return hk_tuning_full(precision)[0]
+
+
+def hk_tuning_full(precision: int = HK_FP32C):
+    """(lines per work item, tile width in bins) currently used for `precision`."""
     v = ctypes.c_int(0)
-    _check("hk_tuning", lib().hk_tuning(int(precision), ctypes.byref(v)))
-    return int(v.value)
+    t = ctypes.c_int(0)
+    _check("hk_tuning", lib().hk_tuning(int(precision), ctypes.byref(v), ctypes.byref(t)))
+    return int(v.value), int(t.value)
 
 
-def hk_set_tuning(precision: int, lmax: int):
-    """Sets the lines-per-item setting of `precision` on the current device."""
-    _check("hk_set_tuning", lib().hk_set_tuning(int(precision), int(lmax)))
+def hk_set_tuning(precision: int, lmax: int, tile_bins: int = 0):
+    """Sets lines per work item (and, unless 0, the tile width) of `precision`
+    on the current device."""
+    _check("hk_set_tuning", lib().hk_set_tuning(int(precision), int(lmax), int(tile_bins)))
 
 
 def hk_sync_status(stream=None):

@@ -3,6 +3,9 @@
 The bar (benchmark statement): relative L1 error <= 1e-5 and per-bin relative
 error <= 1e-4 over the bins where the oracle's sigma exceeds 1e-10 * max(sigma).
 """
+import json
+import os
+
 import numpy as np
 
 L1_TOL = 1e-5
@@ -64,3 +67,12 @@ def oracle_sigma_max(oracle, L, grid, state, cut, top=24, halfwidth=3):
             best = max(best, float(np.max(oracle.cross_section(L.as_oracle(), grid, state, cut,
                                                                 lo, hi))))
     return best
+
+
+def record(what, err):
+    """Appends a measured error to the JSON-lines file named by HK_ERRORS_JSON
+    (unset: nothing is written), for the per-configuration error table."""
+    path = os.environ.get("HK_ERRORS_JSON")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"what": what, **err}) + "\n")

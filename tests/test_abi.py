@@ -98,7 +98,9 @@ def test_new_options_validated_on_host(hk):
     bst = hk.make_state(1000.0, 1.0, 3000.0, P_self=-0.1)
     assert L.hk_cross_section(b(lines), b(grid), b(bst), b(op), 1, None) == hk.HK_EINVAL
     assert L.hk_cross_section_host(b(lines), b(grid), b(st), b(op), 1, -5, None) == hk.HK_EINVAL
-    assert L.hk_set_tuning(hk.HK_FP32C, 8) == hk.HK_EINVAL
-    assert L.hk_set_tuning(7, 2048) == hk.HK_EINVAL
+    assert L.hk_set_tuning(hk.HK_FP32C, 8, 0) == hk.HK_EINVAL
+    assert L.hk_set_tuning(7, 2048, 0) == hk.HK_EINVAL
+    assert L.hk_set_tuning(hk.HK_FP32C, 2048, 1536) == hk.HK_EINVAL   # tile widths: 1024, 2048
+    assert L.hk_set_tuning(hk.HK_FP64, 2048, 1024) == hk.HK_EINVAL    # FP64 tiles: 512
     v = ctypes.c_int(0)
-    assert L.hk_tuning(7, b(v)) == hk.HK_EINVAL
+    assert L.hk_tuning(7, b(v), None) == hk.HK_EINVAL

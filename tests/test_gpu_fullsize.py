@@ -24,7 +24,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import BIN_TOL, L1_TOL, MASK_REL, sigma_errors
+from parity import BIN_TOL, L1_TOL, MASK_REL, record, sigma_errors
 from paper_2101_02005_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -50,14 +50,6 @@ def _free():
     torch.cuda.empty_cache()
 
 
-def record(what, err):
-    """Appends a measured error to the JSON-lines file named by HK_ERRORS_JSON
-    (unset: nothing is written), for the per-configuration error table."""
-    path = os.environ.get("HK_ERRORS_JSON")
-    if path:
-        import json
-        with open(path, "a") as f:
-            f.write(json.dumps({"what": what, **err}) + "\n")
 
 
 def sample_bins(sig, seed, n_rand=16, n_above=24):

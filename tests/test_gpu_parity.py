@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import assert_sigma_close, oracle_sigma_max, sigma_errors
+from parity import assert_sigma_close, oracle_sigma_max, record, sigma_errors
 from paper_2101_02005_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -55,6 +55,7 @@ def test_config0_full(hk, prec):
     ref = oracle_sigma(L, w.grid, T, P, w.cut)
     got = gpu_sigma(hk, L, w.grid, T, P, w.cut, prec)
     e = assert_sigma_close(got, ref, f"c0 prec={prec}")
+    record(f"c0 {'fp64' if prec else 'fp32c'} (whole array)", e)
     # at 1000 K a few high-E'' lines dominate max(sigma); a few % of bins pass the mask
     assert e["n_mask"] > 500
 
@@ -594,10 +595,31 @@ def test_autotune_keeps_results(hk):
             hk.make_opts(QREF, w.cut, flags=hk.HK_SIGMA_F64))
     before = hk.hk_cross_section(*args).cpu().numpy()
     hk.hk_autotune(*args)
-    assert hk.hk_tuning(hk.HK_FP32C) in (1024, 2048, 4096, 16384, 65536)
+    lmax, tile = hk.hk_tuning_full(hk.HK_FP32C)
+    assert lmax in (1024, 2048, 4096, 16384, 65536) and tile in (1024, 2048)
     after = hk.hk_cross_section(*args).cpu().numpy()
     hk.hk_sync_status()
     assert_sigma_close(after, before, "after autotune")
+    hk.hk_set_tuning(hk.HK_FP32C, 2048, 1024)
+
+
+@pytest.mark.parametrize("tile", [1024, 2048])
+def test_tile_widths_match_oracle(hk, tile):
+    """Both tile widths the autotuner chooses from, for short lines (501 bins,
+    tiles with a halo) and wide ones (2001 bins, peeled sweeps), at two
+    lines-per-item settings: parity with the oracle."""
+    try:
+        for lmax in (1024, 65536):
+            hk.hk_set_tuning(hk.HK_FP32C, lmax, tile)
+            for cut in (25.0, 100.0):
+                L = synth.make_lines(6000, 0.0, 800.0, 93, 18.0, windows=8)
+                grid = synth.Grid(0.0, 0.05 if cut > 50 else 0.1, 16000 if cut > 50 else 8000)
+                ref = oracle_sigma(L, grid, 1200.0, 0.7, cut)
+                got = gpu_sigma(hk, L, grid, 1200.0, 0.7, cut, 0, flags=hk.HK_SIGMA_F64)
+                assert_sigma_close(got, ref, f"tile {tile} lmax {lmax} cut {cut}")
+                assert np.array_equal(ref == 0, got == 0)
+    finally:
+        hk.hk_set_tuning(hk.HK_FP32C, 2048, 1024)
 
 
 def test_dense_line_batches(hk):
@@ -607,7 +629,8 @@ def test_dense_line_batches(hk):
     nearest bins in one batch: per-line path), lines so narrow in Doppler
     width that no bin is in their four-node band, lines near the tile edges
     (1024-bin tiles), and a ragged last cluster; FP32C against the oracle,
-    with the oracle's zero pattern."""
+    with the oracle's zero pattern; also lines a hair either side of the
+    half-bins where the halo tiles' ownership changes."""
     rng = np.random.default_rng(2101)
     dnu, nbins = 0.1, 12000
     centres = np.sort(rng.uniform(40.0, 1160.0, 420))
@@ -620,6 +643,9 @@ def test_dense_line_batches(hk):
         elif i % 11 == 5:                    # on a tile edge
             base = (1024 * (1 + i % 10)) * dnu
             offs = rng.uniform(-1e-3, 1e-3, 12)
+        elif i % 13 == 6:                    # where tile ownership changes (a half-bin
+            base = (512 * (1 + i % 20) - 0.5) * dnu   # before a multiple of 512 bins)
+            offs = np.linspace(-2e-9, 2e-9, 8)
         else:                                # one shared nearest bin
             base = k * dnu + rng.uniform(-0.04, 0.04)
             offs = rng.uniform(-2e-3, 2e-3, int(rng.integers(4, 17)))
