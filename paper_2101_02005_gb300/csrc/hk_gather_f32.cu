@@ -62,7 +62,8 @@ struct __align__(16) Rec {
     int ch, Lc, Rc, L2;         // last core bin (core bins: r2 < 64); groups holding core bins;
     int R2;                     //   groups of band gh2 or inner
     float rn, s, y;             // centre offset from bin c, scaled strength, Gamma_L / alpha_D
-    float h, sy2, Yq, pad;      // the plinth s Re w(x_cut + iy) (or 0); sy / 2, Y + 1/4 (2 nodes)
+    float h, k2a, k2b, pad;     // the plinth s Re w(x_cut + iy) (or 0); Y - 1/2, 2 Y (2 nodes;
+                                //   binned Gaussian: sqrt(pi)/(2b) s, b/2)
 };
 static_assert(sizeof(Rec) == 112, "Rec is seven 16-byte quads");
 
@@ -141,8 +142,8 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
     q.y = y;
     q.rnb = q.rn * b;
     q.sy = sy;
-    q.sy2 = 0.5f * sy;
-    q.Yq = Y + 0.25f;
+    q.k2a = Y - 0.5f;
+    q.k2b = 2.0f * Y;
     q.Ca = fmaf(2.0f * kTa, Y, kTa * kTa);
     q.Cb = fmaf(2.0f * kTb, Y, kTb * kTb);
     q.sa = sy * kWa;
@@ -152,8 +153,8 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
               ? sv * profile_rel<float>(g.profile, (float)cw.W * b, y, b)
               : 0.0f;
     if (g.profile == kProfBinned) {          // sqrt(pi)/(2b) s and b/2 in the 2-node slots
-        q.sy2 = sv * (float)(0.5 / kInvSqrtPi) / b;
-        q.Yq = 0.5f * b;
+        q.k2a = sv * (float)(0.5 / kInvSqrtPi) / b;
+        q.k2b = 0.5f * b;
     }
     if (any) {
         q.gA = lo >> 5;
@@ -199,13 +200,13 @@ template <int BAND> __device__ __forceinline__ float pair_raw(const Rec &q, floa
     if (BAND == kBandGauss) {
         return q.s * exp2f(-X * 1.4426950408889634f);
     } else if (BAND == kBandBinned) {
-        const float ax = fabsf(x), a = ax - q.Yq, c = ax + q.Yq;
-        return q.sy2 * (a >= 0.0f ? erfcf(a) - erfcf(c) : erff(c) + erff(-a));
+        const float ax = fabsf(x), a = ax - q.k2b, c = ax + q.k2b;
+        return q.k2a * (a >= 0.0f ? erfcf(a) - erfcf(c) : erff(c) + erff(-a));
     } else if (BAND == kBandGH1) {
         return q.sy * rcp_ftz(r2);
     } else if (BAND == kBandGH2) {          // |z^2 - 1/2|^2 = r2^2 - X + Y + 1/4
-        const float d = fmaf(r2, r2, q.Yq - X);
-        return fmaf(r2, q.sy, q.sy2) * rcp_ftz(d);
+        const float Xp = fmaf(x, x, q.k2a);      // X' = x^2 + Y - 1/2
+        return fmaf(Xp, q.sy, q.sy) * rcp_ftz(fmaf(Xp, Xp, q.k2b));
     } else {                                // 4 nodes: |z^2 - tau|^2 = r2^2 - 2 tau (X - Y) + tau^2
         const float da = fmaf(r2, r2, fmaf(-2.0f * kTa, X, q.Ca));
         const float db = fmaf(r2, r2, fmaf(-2.0f * kTb, X, q.Cb));
@@ -310,7 +311,7 @@ __device__ __forceinline__ void sweep_binned(const Rec &q, int g0, int g1, int l
         if (--g1 < g0) return;
     }
     // lower edge of this lane's bin in group g: x - b/2
-    auto lower = [&](int g) { return fmaf((float)(32 * g + kfc), q.b, -q.rnb) - q.Yq; };
+    auto lower = [&](int g) { return fmaf((float)(32 * g + kfc), q.b, -q.rnb) - q.k2b; };
     float e = lower(g0);
     float E = erfcf(fabsf(e));
     for (int g = g0; g <= g1; ++g) {
@@ -324,7 +325,7 @@ __device__ __forceinline__ void sweep_binned(const Rec &q, int g0, int g1, int l
             Eh = E0;
         }
         const float d = (e >= 0.0f) ? E - Eh : (eh <= 0.0f ? Eh - E : 2.0f - E - Eh);
-        float v = q.sy2 * d;
+        float v = q.k2a * d;
         if (V & kVPlinth) v -= q.h;
         base[32 * (g - tg0)] += v;
         e = en;
@@ -474,15 +475,17 @@ __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1
 // groups reach gA or gB, takes the per-line path.
 constexpr int NLB = 4;
 
-// Two-node value of a pair, as fma(num, 1/d, acc): with X = x^2,
-// d = |z^2 - 1/2|^2 = X^2 + (2Y - 1) X + (Y + 1/2)^2, num = sy (X + Y + 1/2).
-__device__ __forceinline__ float gh2_acc(float kf, float b, float nrb, float B, float C, float sy,
-                                         float E, float acc)
+// Two-node value of a pair, as fma(num, 1/d, acc).  The rule's
+// |z^2 - 1/2|^2 = X^2 + (2Y - 1) X + (Y + 1/2)^2 (X = x^2) is, with
+// X' = x^2 + Y - 1/2, X'^2 + 2Y, and its numerator sy (X + Y + 1/2) is
+// sy (X' + 1): three FMAs and the reciprocal after x (Ym = Y - 1/2, Y2 = 2Y).
+// In the band, x^2 + Y >= 2500, so neither sum cancels.
+__device__ __forceinline__ float gh2_acc(float kf, float b, float nrb, float Ym, float Y2, float sy,
+                                         float acc)
 {
     const float x = fmaf(kf, b, nrb);
-    const float X = x * x;
-    const float d = fmaf(X + B, X, C);
-    return fmaf(fmaf(X, sy, E), rcp_ftz(d), acc);
+    const float Xp = fmaf(x, x, Ym);
+    return fmaf(fmaf(Xp, sy, sy), rcp_ftz(fmaf(Xp, Xp, Y2)), acc);
 }
 
 // Four-node value of a pair (valid for every r2 >= 64); *r2 = x^2 + y^2.
@@ -502,14 +505,14 @@ __device__ __forceinline__ float gh4_val(float kf, float b, float nrb, float Y, 
 // (n0 d1 + n1 d0) / (d0 d1): the same issue count as two reciprocals and half
 // the MUFU work.  The caller bounds r2 (d <= (r2 + 1)^2) so that the products
 // stay in the float range.
-__device__ __forceinline__ float gh2_pair_acc(float kf0, float b0, float nrb0, float B0, float C0,
-                                              float sy0, float E0, float kf1, float b1, float nrb1,
-                                              float B1, float C1, float sy1, float E1, float acc)
+__device__ __forceinline__ float gh2_pair_acc(float kf0, float b0, float nrb0, float Ym0, float Y20,
+                                              float sy0, float kf1, float b1, float nrb1, float Ym1,
+                                              float Y21, float sy1, float acc)
 {
     const float x0 = fmaf(kf0, b0, nrb0), x1 = fmaf(kf1, b1, nrb1);
-    const float X0 = x0 * x0, X1 = x1 * x1;
-    const float d0 = fmaf(X0 + B0, X0, C0), d1 = fmaf(X1 + B1, X1, C1);
-    const float n0 = fmaf(X0, sy0, E0), n1 = fmaf(X1, sy1, E1);
+    const float X0 = fmaf(x0, x0, Ym0), X1 = fmaf(x1, x1, Ym1);
+    const float d0 = fmaf(X0, X0, Y20), d1 = fmaf(X1, X1, Y21);
+    const float n0 = fmaf(X0, sy0, sy0), n1 = fmaf(X1, sy1, sy1);
     return fmaf(fmaf(n0, d1, n1 * d0), rcp_ftz(d0 * d1), acc);
 }
 
@@ -569,17 +572,15 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
         return 0u;
     }
     if (max(gA, tg0) > min(gB, tg1)) return 0u;
-    float b[NLB], nrb[NLB], B[NLB], C[NLB], sy[NLB], E[NLB];
+    float b[NLB], nrb[NLB], Ym[NLB], Y2[NLB], sy[NLB];
 #pragma unroll
     for (int j = 0; j < NLB; ++j) {
         const float4 t = quadf(R[j], 0);   // (b, rn b, Y, sy)
         b[j] = t.x;
         nrb[j] = -t.y;              // x = (k - rn) b, the per-line path's arithmetic
-        const float Yh = t.z + 0.5f;
-        B[j] = fmaf(2.0f, t.z, -1.0f);
-        C[j] = Yh * Yh;
+        Ym[j] = t.z - 0.5f;
+        Y2[j] = 2.0f * t.z;
         sy[j] = t.w;
-        E[j] = t.w * Yh;
     }
     const int kfc = lane - c0;
     // the two-node rule over [g0, g1] (clipped to the tile), unmasked
@@ -594,7 +595,7 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
             float v0 = 0.0f;
 #pragma unroll
             for (int j = 0; j < NLB; ++j)
-                v0 = gh2_acc(kf, b[j], nrb[j], B[j], C[j], sy[j], E[j], v0);
+                v0 = gh2_acc(kf, b[j], nrb[j], Ym[j], Y2[j], sy[j], v0);
             p[0] += v0;
         }
     };
@@ -606,7 +607,7 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
         float v = 0.0f;
 #pragma unroll
         for (int j = 0; j < NLB; ++j) {
-            const float t = gh2_acc(kf, b[j], nrb[j], B[j], C[j], sy[j], E[j], 0.0f);
+            const float t = gh2_acc(kf, b[j], nrb[j], Ym[j], Y2[j], sy[j], 0.0f);
             v += (bin >= R[j].lo && bin <= R[j].hi) ? t : 0.0f;
         }
         base[32 * (g - tg0)] += v;
@@ -750,7 +751,7 @@ __device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0
         }
         return;
     }
-    float kf[NLB], b[NLB], nrb[NLB], P1[NLB], P2[NLB], sy[NLB], P3[NLB];
+    float kf[NLB], b[NLB], nrb[NLB], P1[NLB], P2[NLB], sy[NLB];
     float H = 0.0f;
 #pragma unroll
     for (int j = 0; j < NLB; ++j) {
@@ -758,10 +759,9 @@ __device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0
         b[j] = R[j].b;
         nrb[j] = -R[j].rnb;
         sy[j] = R[j].sy;
-        const float Y = R[j].Y, Yh = Y + 0.5f;
-        P1[j] = cls == 1 ? Y : fmaf(2.0f, Y, -1.0f);
-        P2[j] = Yh * Yh;
-        P3[j] = sy[j] * Yh;
+        const float Y = R[j].Y;
+        P1[j] = cls == 1 ? Y : Y - 0.5f;   // one node: r2 = x^2 + Y; two nodes: Y - 1/2
+        P2[j] = 2.0f * Y;
         if (V & kVPlinth) H += R[j].h;
     }
     // pairs of lines share a reciprocal when every r2 of the tile stays below
@@ -803,8 +803,8 @@ __device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0
             float v = -H;
 #pragma unroll
             for (int j = 0; j < NLB; j += 2) {
-                v = gh2_pair_acc(kf[j], b[j], nrb[j], P1[j], P2[j], sy[j], P3[j], kf[j + 1],
-                                 b[j + 1], nrb[j + 1], P1[j + 1], P2[j + 1], sy[j + 1], P3[j + 1], v);
+                v = gh2_pair_acc(kf[j], b[j], nrb[j], P1[j], P2[j], sy[j], kf[j + 1], b[j + 1],
+                                 nrb[j + 1], P1[j + 1], P2[j + 1], sy[j + 1], v);
                 kf[j] += 32.0f;
                 kf[j + 1] += 32.0f;
             }
@@ -815,7 +815,7 @@ __device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0
             float v = -H;
 #pragma unroll
             for (int j = 0; j < NLB; ++j) {
-                v = gh2_acc(kf[j], b[j], nrb[j], P1[j], P2[j], sy[j], P3[j], v);
+                v = gh2_acc(kf[j], b[j], nrb[j], P1[j], P2[j], sy[j], v);
                 kf[j] += 32.0f;
             }
             p[0] += v;
