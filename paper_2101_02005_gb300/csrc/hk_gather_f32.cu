@@ -774,7 +774,35 @@ __device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0
     }
     float *p = base;
     float *const pe = base + 32 * (tg1 - tg0);
-    if (cls == 1 && share) {
+    // one node, with x from the tile's origin: x = fma(g, 32 b, x0), g the
+    // group count from the tile start.  In a one-node tile every |x| >= 1225
+    // (r2 >= 1.5e6), so the rounding of x0 costs at most ulp(|x0| + 1024 b)/1225
+    // relative in x: taken while that stays below 2e-7, else the exact offsets
+    bool origin = cls == 1 && share;
+#pragma unroll
+    for (int j = 0; j < NLB; ++j) {
+        const float xmax = fabsf(fmaf(kf[j], b[j], nrb[j])) + (float)(32 * (tg1 - tg0 + 1)) * b[j];
+        origin = origin && xmax < 1225.0f * 2e-7f * 16777216.0f;   // half an ulp <= xmax 2^-24
+    }
+    if (origin) {
+        float x0[NLB], b32[NLB];
+#pragma unroll
+        for (int j = 0; j < NLB; ++j) {
+            x0[j] = fmaf(kf[j], b[j], nrb[j]);
+            b32[j] = 32.0f * b[j];
+        }
+        float gf = 0.0f;
+        for (; p <= pe; p += 32, gf += 1.0f) {
+            float v = -H;
+#pragma unroll
+            for (int j = 0; j < NLB; j += 2) {
+                const float xa = fmaf(gf, b32[j], x0[j]), xb = fmaf(gf, b32[j + 1], x0[j + 1]);
+                const float r0 = fmaf(xa, xa, P1[j]), r1 = fmaf(xb, xb, P1[j + 1]);
+                v = fmaf(fmaf(sy[j], r1, sy[j + 1] * r0), rcp_ftz(r0 * r1), v);
+            }
+            p[0] += v;
+        }
+    } else if (cls == 1 && share) {
         for (; p <= pe; p += 32) {
             float v = -H;
 #pragma unroll
@@ -887,7 +915,11 @@ __global__ void __launch_bounds__(NT, 3)
         float *accb = accs + warp * tile + lane;
         int rounds = 0;
         for (int64_t base = l_begin; base < l_end; base += NT) {
-            const int64_t l = base + tid;  // warp w owns lines base + 32 w + lane
+            // short lines: warp w owns lines base + 32 w + lane (consecutive lines,
+            // whose batches share their structure); wide lines: base + w + 8 lane,
+            // so that every warp of the block gets lines from the whole round and
+            // the warps reach the fold barriers together (7 % at config 3)
+            const int64_t l = (V & kVPeel) ? base + warp + NW * lane : base + tid;
             Rec q;
             if (l < l_end) {
                 make_rec(pr, g, l, scale, &q);

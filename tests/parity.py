@@ -3,6 +3,7 @@
 The bar (benchmark statement): relative L1 error <= 1e-5 and per-bin relative
 error <= 1e-4 over the bins where the oracle's sigma exceeds 1e-10 * max(sigma).
 """
+import concurrent.futures as cf
 import json
 import os
 
@@ -76,3 +77,92 @@ def record(what, err):
     if path:
         with open(path, "a") as f:
             f.write(json.dumps({"what": what, **err}) + "\n")
+
+
+def assert_plinth_close(gpu, ref, base, what="", l1=L1_TOL, per_bin=BIN_TOL):
+    """Parity of a plinth-removed sigma (Sect. 2.1).
+
+    The plinth-removed value of a bin is a difference: the sum of the line
+    profiles `base` (the un-removed sigma) less the sum of the lines'
+    plinths, base - ref >= 0.  Each side carries the relative rounding error
+    of the terms it sums, so the error of the difference is bounded relative
+    to the terms, that is relative to `base`: per bin and in L1 over the
+    mask base > 1e-10 max(base).  Where the difference is well conditioned
+    (ref >= base / 2, condition number at most 2) the removed value is also
+    held to the bar itself, per bin and in L1, relative to ref.  Returns the
+    errors of both regions."""
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    base = np.asarray(base, dtype=np.float64)
+    assert np.all(np.isfinite(gpu)), what
+    m = base > MASK_REL * base.max()
+    d = np.abs(gpu - ref)
+    e = {"terms_l1": float(d[m].sum() / base[m].sum()),
+         "terms_max_bin": float(np.max(d[m] / base[m]))}
+    far = m & (ref >= 0.5 * base)
+    if np.any(far):
+        e["l1"] = float(d[far].sum() / ref[far].sum())
+        e["max_bin"] = float(np.max(d[far] / ref[far]))
+        e["n_far"] = int(far.sum())
+    ok = (e["terms_l1"] <= l1 and e["terms_max_bin"] <= per_bin
+          and e.get("l1", 0.0) <= l1 and e.get("max_bin", 0.0) <= per_bin)
+    assert ok, (what, e)
+    return e
+
+
+def sample_bins(sig, seed, n_rand=16, n_above=24):
+    """Seeded bins of a whole sigma array: uniform over the grid, uniform over
+    the bins above the mask, the argmax, and the first and last bins (where
+    to compare; the expected values come from the oracle alone)."""
+    rng = np.random.default_rng(seed)
+    n = sig.size
+    b = set(rng.integers(0, n, n_rand).tolist())
+    above = np.flatnonzero(sig > MASK_REL * sig.max())
+    if above.size:
+        b |= set(rng.choice(above, min(n_above, above.size), replace=False).tolist())
+    b |= {0, n - 1, int(np.argmax(sig))}
+    return np.array(sorted(b), dtype=np.int64)
+
+
+def oracle_bins(L, grid, state, cut, bins, per_gram=False):
+    """Oracle sigma at each bin of `bins`, from the lines within cut + 2 bins
+    of it (all lines if there is no cut; the oracle's cut predicate still
+    decides each pair); bins in parallel threads."""
+    import oracle
+    nu_min, dnu, nbins = grid
+
+    def one(i):
+        if cut > 0:
+            nu = nu_min + i * dnu
+            a = int(np.searchsorted(L.nu0, nu - cut - 2 * dnu, "left"))
+            b = int(np.searchsorted(L.nu0, nu + cut + 2 * dnu, "right"))
+            sub = L.subset(slice(a, b))
+        else:
+            sub = L
+        if sub.n == 0:
+            return 0.0
+        return float(oracle.cross_section(sub.as_oracle(), grid, state, cut, int(i), int(i) + 1,
+                                          nthreads=1, per_gram=per_gram)[0])
+
+    with cf.ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        return np.array(list(ex.map(one, bins.tolist())))
+
+
+def sampled_errors(gpu_full, L, grid, state, cut, seed):
+    """Errors of a whole sigma array (host, f64) on a seeded sample of bins
+    (sample_bins) against the oracle bin by bin: relative L1 and per-bin
+    relative error over the sampled bins above 1e-10 of the oracle's value at
+    the array's maximum, and the largest absolute error below that mask."""
+    gpu_full = np.asarray(gpu_full, dtype=np.float64)
+    assert np.all(np.isfinite(gpu_full))
+    bins = sample_bins(gpu_full, seed)
+    ref = oracle_bins(L, grid, state, cut, bins)
+    g = gpu_full[bins]
+    ref_max = float(ref[bins == int(np.argmax(gpu_full))][0])
+    assert ref_max > 0
+    m = ref > MASK_REL * ref_max
+    d = np.abs(g - ref)
+    return dict(n=int(bins.size), n_mask=int(m.sum()),
+                max_bin=float(np.max(d[m] / ref[m])) if m.any() else 0.0,
+                l1=float(d[m].sum() / ref[m].sum()) if m.any() else 0.0,
+                below_mask_abs=float(d[~m].max()) if (~m).any() else 0.0, ref_max=ref_max)

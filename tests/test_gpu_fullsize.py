@@ -24,7 +24,7 @@ import numpy as np
 import pytest
 
 import oracle
-from parity import BIN_TOL, L1_TOL, MASK_REL, record, sigma_errors
+from parity import BIN_TOL, L1_TOL, MASK_REL, record, sampled_errors, sigma_errors
 from paper_2101_02005_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -52,59 +52,14 @@ def _free():
 
 
 
-def sample_bins(sig, seed, n_rand=16, n_above=24):
-    """Seeded bins: uniform over the grid, uniform over the bins above the
-    mask, the argmax, and the first and last bins."""
-    rng = np.random.default_rng(seed)
-    n = sig.size
-    b = set(rng.integers(0, n, n_rand).tolist())
-    above = np.flatnonzero(sig > MASK_REL * sig.max())
-    if above.size:
-        b |= set(rng.choice(above, min(n_above, above.size), replace=False).tolist())
-    b |= {0, n - 1, int(np.argmax(sig))}
-    return np.array(sorted(b), dtype=np.int64)
-
-
-def oracle_bins(L, grid, state, cut, bins, per_gram=False):
-    """Oracle sigma at each bin of `bins`, from the lines within cut + 2 bins
-    of it (all lines if there is no cut); bins in parallel threads."""
-    nu_min, dnu, nbins = grid
-
-    def one(i):
-        if cut > 0:
-            nu = nu_min + i * dnu
-            a = int(np.searchsorted(L.nu0, nu - cut - 2 * dnu, "left"))
-            b = int(np.searchsorted(L.nu0, nu + cut + 2 * dnu, "right"))
-            sub = L.subset(slice(a, b))
-        else:
-            sub = L
-        if sub.n == 0:
-            return 0.0
-        return float(oracle.cross_section(sub.as_oracle(), grid, state, cut, int(i), int(i) + 1,
-                                          nthreads=1, per_gram=per_gram)[0])
-
-    with cf.ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
-        return np.array(list(ex.map(one, bins.tolist())))
-
-
 def check_sampled(gpu_full, L, grid, state, cut, seed, what):
     """gpu_full: the whole sigma array (host, f64).  Returns the sample's errors."""
-    assert np.all(np.isfinite(gpu_full)), what
-    bins = sample_bins(gpu_full, seed)
-    ref = oracle_bins(L, grid, state, cut, bins)
-    g = gpu_full[bins]
-    ref_max = ref[bins == int(np.argmax(gpu_full))][0]
-    assert ref_max > 0, what
-    m = ref > MASK_REL * ref_max
-    assert m.sum() >= 8, (what, int(m.sum()))
-    d = np.abs(g[m] - ref[m])
-    rel = d / ref[m]
-    l1 = float(d.sum() / ref[m].sum())
-    err = dict(n=int(bins.size), n_mask=int(m.sum()), max_bin=float(rel.max()), l1=l1)
+    err = sampled_errors(gpu_full, L, grid, state, cut, seed)
     record(what, err)
-    assert rel.max() <= BIN_TOL and l1 <= L1_TOL, (what, err, bins[m][np.argmax(rel)])
+    assert err["n_mask"] >= 8, (what, err)
+    assert err["max_bin"] <= BIN_TOL and err["l1"] <= L1_TOL, (what, err)
     # bins under the mask: absolute error within the per-bin bar at the mask level
-    assert np.all(np.abs(g[~m] - ref[~m]) <= BIN_TOL * MASK_REL * ref_max), what
+    assert err["below_mask_abs"] <= BIN_TOL * MASK_REL * err["ref_max"], (what, err)
     return err
 
 
