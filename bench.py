@@ -61,6 +61,9 @@ def parse():
                          "workload (config 4) instead of the forward step")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched config-3 launch that follows the headline step")
+    ap.add_argument("--table", default=None, metavar="CONFIGS",
+                    help="per-configuration throughput table instead of the headline: "
+                         "comma-separated config numbers (0-4), one JSON line per entry")
     ap.add_argument("--batched", action="store_true",
                     help="time one hk_cross_section_batched launch over every species x "
                          "(T, P) point of the workload (config 3) per step")
@@ -151,9 +154,11 @@ def smi_gpu_id(dev):
 
 def measure_peaks(hk, dev, ms=1000.0):
     """Measured pipe throughputs of this GPU (hk_measure_peak), each with the
-    SM clock sampled while it ran: FP32 FMA, MUFU reciprocal, FP64 FMA."""
+    SM clock sampled while it ran: FP32 FMA, MUFU reciprocal and exp2, FP64
+    FMA (lane operations per second)."""
     out = {}
-    for kind, name in [(hk.PEAK_FFMA, "ffma"), (hk.PEAK_RCP, "mufu_rcp"), (hk.PEAK_DFMA, "dfma")]:
+    for kind, name in [(hk.PEAK_FFMA, "ffma"), (hk.PEAK_RCP, "mufu_rcp"), (hk.PEAK_EX2, "mufu_ex2"),
+                       (hk.PEAK_DFMA, "dfma")]:
         hk.hk_measure_peak(kind, 100.0)
         s = ClockSampler(smi_gpu_id(dev))
         s.start()
@@ -421,6 +426,142 @@ def batched_measure(w, hk, synth, dev, steps, warmup, peaks):
     return out_
 
 
+def run_table(args, hk, synth, dev):
+    """Throughput of every configuration (0-4) at its full size, one JSON line
+    per entry: the FP32-compensated path (device-resident lines, sigma in FP64)
+    and the plain FP64 GPU form (on an every-k-th-line sample where the full
+    list would take minutes; a line's work does not depend on the density),
+    each with its own autotuned lines per work item (FP64: tuned on at most
+    5e6 lines of the list), SM clocks sampled during the timed launches, and
+    the oracle's pairs/s on seeded windows (config 0: the whole array).  The
+    per-configuration errors against the oracle come from the full-size GPU
+    tests, which record them."""
+    import torch
+    Q = synth.partition_function
+    qref = float(Q(296.0))
+    only = [int(c) for c in args.table.split(",") if c.strip()]
+
+    def emit(d):
+        print(json.dumps(d), flush=True)
+
+    def timed(fn, reps, warm=2):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        smp = ClockSampler(smi_gpu_id(dev))
+        smp.start()
+        time.sleep(0.25)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        c = smp.stop()
+        hk.hk_sync_status()
+        return e0.elapsed_time(e1) / reps, c
+
+    def single(tag, L, grid_t, T, P, cut, prec, reps, every=None):
+        Ls = L if every is None else L.subset(slice(0, None, every))
+        D = hk.DeviceLines.from_host(Ls)
+        grid = hk.make_grid(*grid_t)
+        st = hk.make_state(T, P, float(Q(T)))
+        op = hk.make_opts(qref, cut, prec, flags=hk.HK_SIGMA_F64 if prec == hk.HK_FP32C else 0)
+        out = torch.empty(grid_t[2], dtype=torch.float64, device=dev)
+        if prec == hk.HK_FP64 and Ls.n > 5_000_000:
+            Dt = hk.DeviceLines.from_host(Ls.subset(slice(0, None, -(-Ls.n // 5_000_000))))
+            hk.hk_autotune(Dt, grid, st, op)
+            del Dt
+        else:
+            hk.hk_autotune(D, grid, st, op)
+        pairs = hk.hk_count_pairs(D, grid, st, op)[0]
+        ms, c = timed(lambda: hk.hk_cross_section(D, grid, st, op, out), reps)
+        emit({"table": tag, "precision": "fp64" if prec else "fp32c", "lines": Ls.n,
+              "sample": f"every {every}th line" if every else "all lines", "ms": ms,
+              "lines_per_s": Ls.n / (ms / 1e3), "evals_per_s": pairs / (ms / 1e3),
+              "pairs": pairs, "tuning": hk.hk_tuning_full(prec),
+              "sm_mhz": c.get("sm_mhz"), "reasons": c.get("reasons")})
+        del D, out
+        torch.cuda.empty_cache()
+
+    def oracle_rate(tag, w, L, T, P, secs=8.0):
+        rate, t_used, pairs, wins = cpu_sample(w, L, T, P, seconds_target=secs)
+        emit({"table": tag, "oracle_pairs_per_s": rate, "cores": os.cpu_count(),
+              "pairs": pairs, "seconds": t_used, "sample": sample_text(wins, pairs, t_used)})
+
+    if 0 in only:
+        w = synth.config(0)
+        L = w.species[0]
+        T, P = w.states()[0]
+        for prec in (hk.HK_FP32C, hk.HK_FP64):
+            single("c0", L, w.grid.astuple(), T, P, w.cut, prec, 20)
+        import oracle
+        t0 = time.perf_counter()
+        oracle.cross_section(L.as_oracle(), w.grid.astuple(), (T, P, float(Q(T)), qref), w.cut)
+        dt = time.perf_counter() - t0
+        emit({"table": "c0 oracle (whole array)", "seconds": dt, "cores": os.cpu_count(),
+              "oracle_pairs_per_s": oracle.count_pairs(L.nu0, *w.grid.astuple(), w.cut) / dt})
+    if 1 in only:
+        w = synth.config(1)
+        L = w.species[0]
+        T, P = w.states()[0]
+        single("c1", L, w.grid.astuple(), T, P, w.cut, hk.HK_FP32C, 5)
+        single("c1", L, w.grid.astuple(), T, P, w.cut, hk.HK_FP64, 1, every=10)
+        oracle_rate("c1 oracle", w, L, T, P)
+        del w, L
+    if 2 in only:
+        w = synth.config(2)
+        L = w.species[0]
+        T, P = w.states()[0]
+        single("c2 molecules", L, w.grid.astuple(), T, P, w.cut, hk.HK_FP32C, 3)
+        single("c2 molecules", L, w.grid.astuple(), T, P, w.cut, hk.HK_FP64, 1, every=100)
+        oracle_rate("c2 molecules oracle", w, L, T, P)
+        A = w.extra["atoms"]
+        ag = w.extra["atom_grid"].astuple()
+        single("c2 atoms", A, ag, T, P, 0.0, hk.HK_FP32C, 3)
+        single("c2 atoms", A, ag, T, P, 0.0, hk.HK_FP64, 1, every=100)
+        del w, L, A
+    if 3 in only:
+        w = synth.config(3)
+        T, P = w.T[10], w.P[5]
+        for s_, L in enumerate(w.species):
+            single(f"c3 species {s_} one point", L, w.grid.astuple(), T, P, w.cut,
+                   hk.HK_FP64, 1, every=10 if L.n > 1e6 else None)
+        oracle_rate("c3 species 3 oracle (one point)", w, w.species[3], T, P)
+        del w
+    if 4 in only:
+        w = synth.config(4)
+        L = w.species[0]
+        pts = w.states()
+        D = hk.DeviceLines.from_host(L)
+        grid = hk.make_grid(*w.grid.astuple())
+        states = [hk.make_state(t, p, float(Q(t)), float(synth.dlnQ_dT(t))) for t, p in pts]
+        op = hk.make_opts(qref, w.cut, hk.HK_FP32C, flags=hk.HK_SIGMA_F64)
+        hk.hk_autotune(D, grid, states[len(states) // 2], op)
+        out = torch.empty((1, len(pts), w.grid.nbins), dtype=torch.float64, device=dev)
+        ws = torch.empty(hk.hk_workspace_size(0, [D], len(pts), grid, op), dtype=torch.uint8,
+                         device=dev)
+        pairs = sum(hk.hk_count_pairs(D, grid, st_, op)[0] for st_ in states)
+        ms, c = timed(lambda: hk.hk_cross_section_batched([D], states, grid, op, out, ws), 3)
+        emit({"table": "c4 forward (16 points, batched)", "precision": "fp32c", "ms": ms,
+              "lines_per_s": L.n * len(pts) / (ms / 1e3), "evals_per_s": pairs / (ms / 1e3),
+              "sm_mhz": c.get("sm_mhz"), "reasons": c.get("reasons")})
+        g = torch.from_numpy(synth.upstream_grad(len(pts), w.grid.nbins,
+                                                 synth.SEED_BASE + 4)).to(dev)
+        ms, c = timed(lambda: hk.hk_cross_section_backward(D, grid, states,
+                                                           hk.make_opts(qref, w.cut), g), 3)
+        emit({"table": "c4 adjoint (16 points)", "ms": ms,
+              "line_points_per_s": L.n * len(pts) / (ms / 1e3),
+              "derivative_evals_per_s": pairs / (ms / 1e3), "sm_mhz": c.get("sm_mhz"),
+              "reasons": c.get("reasons")})
+        del D, out, ws, g
+        torch.cuda.empty_cache()
+        T, P = pts[5]
+        single("c4 one point", L, w.grid.astuple(), T, P, w.cut, hk.HK_FP64, 1)
+        oracle_rate("c4 oracle (point 5)", w, L, T, P)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -444,6 +585,9 @@ def main():
     pbuild.build()
     from paper_2101_02005_gb300 import hk, synth
 
+    if args.table is not None:
+        run_table(args, hk, synth, dev)
+        return
     peaks_m = measure_peaks(hk, dev)
     t_gen = time.perf_counter()
     w = workload(args)
@@ -573,6 +717,15 @@ def main():
                              D.n_T[sub].contiguous(), L.mass_amu)
         o64 = hk.make_opts(float(Q(296.0)), w.cut, hk.HK_FP64)
         s64 = torch.empty(w.grid.nbins, dtype=torch.float64, device=dev)
+        # the FP64 form's own lines per work item, from the autotuner on every
+        # 10th line of the sample (untimed)
+        sub10 = slice(0, None, 10)
+        Dt = hk.DeviceLines(D64.nu0[sub10].contiguous(), D64.S_ref[sub10].contiguous(),
+                            D64.E_low[sub10].contiguous(), D64.gamma_ref[sub10].contiguous(),
+                            D64.n_T[sub10].contiguous(), L.mass_amu)
+        hk.hk_autotune(Dt, grid, state, o64)
+        del Dt
+        lmax64 = hk.hk_tuning_full(hk.HK_FP64)[0]
         hk.hk_cross_section(D64, grid, state, o64, s64)
         torch.cuda.synchronize()
         hk.hk_profile(1)
@@ -589,7 +742,7 @@ def main():
                       zip(["gh1", "gh2", "gh3", "gh4", "core"], c64[1:]))
         achieved64 = flops64 / (g64_ms / 1e3) / 1e12
         peak64 = 2.0 * peaks_m["dfma"]["ops_per_s"] / 1e12
-        fp64 = {"value": D64.n / (f64ms / 1e3), "unit": "lines/s",
+        fp64 = {"value": D64.n / (f64ms / 1e3), "unit": "lines/s", "lmax_autotuned": lmax64,
                 "voigt_evals_per_s": c64[0] / (f64ms / 1e3), "ms": f64ms,
                 "sample": "every 10th line of the list, one step; every line admits the same "
                           "2 cut/dnu + 1 bins whatever the density, so the whole list takes "

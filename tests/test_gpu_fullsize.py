@@ -253,5 +253,14 @@ def test_config4_full_backward(hk):
     hk.hk_sync_status()
     check_sampled(s.cpu().numpy(), L, w.grid.astuple(), (t, p, float(Q(t)), QREF), w.cut, 45,
                   "c4 fp64 forward")
-    del D
+    del s
+    # the FP32C forward of all 16 points in one batched launch, at three points
+    out = hk.hk_cross_section_batched([D], states, grid,
+                                      hk.make_opts(QREF, w.cut, hk.HK_FP32C, flags=hk.HK_SIGMA_F64))
+    hk.hk_sync_status()
+    for k in (0, 5, 15):
+        t, p = pts[k]
+        check_sampled(out[0, k].cpu().numpy(), L, w.grid.astuple(), (t, p, float(Q(t)), QREF),
+                      w.cut, 460 + k, f"c4 fp32c forward point {k} (batched)")
+    del D, out
     _free()
