@@ -39,9 +39,10 @@ METRIC = "lines/s and Voigt evals/s on 1 GB300 (FP32-comp vs FP64 GPU) at stated
 # the one-node rule's 8 flops there, so it under-reports rather than inflates.
 FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 25, "gh4": 25, "core": 200}
 # DRAM bytes per line of one k_gather_f32 launch, from the ncu capture in
-# profiles/k_gather_f32_config1-1e7-lines.md (246.2 MB for 1e7 lines; traffic
-# grows with the line count).  Set to None when the kernel changes.
-GATHER_DRAM_BYTES_PER_LINE = None
+# profiles/k_gather_f32_config1-1e7-lines.md (241.5 MB read + 4.5 MB written for
+# 1e7 lines; the line list is read once, so traffic grows with the line
+# count).  Set to None when the kernel changes.
+GATHER_DRAM_BYTES_PER_LINE = 24.60
 FP32_LANES_PER_SM = 128
 
 
@@ -63,7 +64,8 @@ def parse():
                     help="skip the batched config-3 launch that follows the headline step")
     ap.add_argument("--table", default=None, metavar="CONFIGS",
                     help="per-configuration throughput table instead of the headline: "
-                         "comma-separated config numbers (0-4), one JSON line per entry")
+                         "comma-separated config numbers (0-4) and 1x (the options on the "
+                         "config-1 list), one JSON line per entry")
     ap.add_argument("--batched", action="store_true",
                     help="time one hk_cross_section_batched launch over every species x "
                          "(T, P) point of the workload (config 3) per step")
@@ -439,7 +441,8 @@ def run_table(args, hk, synth, dev):
     import torch
     Q = synth.partition_function
     qref = float(Q(296.0))
-    only = [int(c) for c in args.table.split(",") if c.strip()]
+    keys = [c.strip() for c in args.table.split(",") if c.strip()]
+    only = [int(c) for c in keys if c.isdigit()]
 
     def emit(d):
         print(json.dumps(d), flush=True)
@@ -510,6 +513,37 @@ def run_table(args, hk, synth, dev):
         single("c1", L, w.grid.astuple(), T, P, w.cut, hk.HK_FP64, 1, every=10)
         oracle_rate("c1 oracle", w, L, T, P)
         del w, L
+    if "1x" in keys:
+        # the options of Sect. 2.1 and 2.4.3 on the config-1 list, one call each
+        # (autotuned per option set): plinth, per-line cuts, other profiles
+        w = synth.config(1)
+        L = w.species[0]
+        T, P = w.states()[0]
+        D = hk.DeviceLines.from_host(L)
+        grid = hk.make_grid(*w.grid.astuple())
+        st = hk.make_state(T, P, float(Q(T)))
+        out = torch.empty(w.grid.nbins, dtype=torch.float64, device=dev)
+        modes = [("Voigt, cut 25", {}),
+                 ("Voigt, plinth removed", {"flags": hk.HK_REMOVE_PLINTH}),
+                 ("Voigt, cut 1000 Doppler widths", {"cut_mode": hk.HK_CUT_DOPPLER, "cut": 1000.0}),
+                 ("Voigt, cut 500 Lorentz widths", {"cut_mode": hk.HK_CUT_LORENTZ, "cut": 500.0}),
+                 ("Lorentzian, cut 25", {"profile": hk.HK_PROFILE_LORENTZ}),
+                 ("Doppler, cut 25", {"profile": hk.HK_PROFILE_DOPPLER}),
+                 ("binned Gaussian, cut 25", {"profile": hk.HK_PROFILE_BINNED_GAUSS})]
+        for name, kw in modes:
+            kw = dict(kw)
+            cut = kw.pop("cut", w.cut)
+            flags = kw.pop("flags", 0) | hk.HK_SIGMA_F64
+            op = hk.make_opts(qref, cut, hk.HK_FP32C, flags=flags, **kw)
+            hk.hk_autotune(D, grid, st, op)
+            pairs = hk.hk_count_pairs(D, grid, st, op)[0]
+            ms, c = timed(lambda: hk.hk_cross_section(D, grid, st, op, out), 3)
+            emit({"table": f"c1 option: {name}", "precision": "fp32c", "lines": L.n, "ms": ms,
+                  "lines_per_s": L.n / (ms / 1e3), "evals_per_s": pairs / (ms / 1e3),
+                  "pairs": pairs, "tuning": hk.hk_tuning_full(hk.HK_FP32C),
+                  "sm_mhz": c.get("sm_mhz"), "reasons": c.get("reasons")})
+        del D, out, w, L
+        torch.cuda.empty_cache()
     if 2 in only:
         w = synth.config(2)
         L = w.species[0]
@@ -666,7 +700,11 @@ def main():
     roofline.update({
         "kernel": ("k_gather_f32<0> (batched short-line sweeps)"
                    if 2 * w.cut / w.grid.dnu + 1 < 1024 else "k_gather_f32<1> (peeled sweeps)"),
-        "traffic": traffic, "algorithmic_bytes": 24 * L.n, "gather_ms_per_launch": g_ms,
+        "traffic": traffic,
+        "traffic_basis": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 1e7-line "
+                          "launch of this kernel (profiles/k_gather_f32_config1-1e7-lines.md), "
+                          "24.6 B per line, scaled by the line count" if traffic else None),
+        "algorithmic_bytes": 24 * L.n, "gather_ms_per_launch": g_ms,
         "gather_share_of_step": g_ms / ms_step if ms_step else None,
         "flops_per_step": flops_step, "cost_model": FLOPS_PER_PAIR,
         "measured_peaks": peaks_m})
