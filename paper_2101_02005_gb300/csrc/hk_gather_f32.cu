@@ -583,6 +583,13 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
         sy[j] = t.w;
     }
     const int kfc = lane - c0;
+    // the plinths: every line of the batch is inside its cut in the interior
+    // groups, so they subtract the batch's sum of plinths there
+    float H = 0.0f;
+    if (V & kVPlinth) {
+#pragma unroll
+        for (int j = 0; j < NLB; ++j) H += R[j].h;
+    }
     // the two-node rule over [g0, g1] (clipped to the tile), unmasked
     auto interior = [&](int g0, int g1) {
         g0 = max(g0, tg0);
@@ -592,7 +599,7 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
         float *p = base + 32 * (g0 - tg0);
         float *const pe = base + 32 * (g1 - tg0);
         for (; p <= pe; p += 32, kf += 32.0f) {
-            float v0 = 0.0f;
+            float v0 = -H;
 #pragma unroll
             for (int j = 0; j < NLB; ++j)
                 v0 = gh2_acc(kf, b[j], nrb[j], Ym[j], Y2[j], sy[j], v0);
@@ -607,7 +614,8 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
         float v = 0.0f;
 #pragma unroll
         for (int j = 0; j < NLB; ++j) {
-            const float t = gh2_acc(kf, b[j], nrb[j], Ym[j], Y2[j], sy[j], 0.0f);
+            float t = gh2_acc(kf, b[j], nrb[j], Ym[j], Y2[j], sy[j], 0.0f);
+            if (V & kVPlinth) t -= R[j].h;
             v += (bin >= R[j].lo && bin <= R[j].hi) ? t : 0.0f;
         }
         base[32 * (g - tg0)] += v;
@@ -639,7 +647,8 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
             const float4 f = quadf(R[j], 1);   // (Ca, Cb, sa, sb)
             const int cl = quadi(R[j], 3).w, ch = quadi(R[j], 4).x;
             float r2;
-            const float t = gh4_val(kf, b[j], nrb[j], quadf(R[j], 0).z, f.x, f.y, f.z, f.w, &r2);
+            float t = gh4_val(kf, b[j], nrb[j], quadf(R[j], 0).z, f.x, f.y, f.z, f.w, &r2);
+            if (V & kVPlinth) t -= R[j].h;   // (the core bins subtract it in the core pass)
             v += (bin >= cl && bin <= ch) ? 0.0f : t;
         }
         p[0] += v;
@@ -932,7 +941,7 @@ __global__ void __launch_bounds__(NT, 3)
             S.rec[warp][lane] = q;
             __syncwarp();
             int qn = 0;
-            if (V == 0) {
+            if ((V & ~kVPlinth) == 0) {   // short Voigt lines, with or without the plinth
                 unsigned rmask = 0u;
                 for (int j0 = 0; j0 < 32; j0 += NLB)
                     rmask |= do_batch<V>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0) << j0;

@@ -326,15 +326,15 @@ struct GridD {
     int halo;                   // FP32C short lines: tile halo in bins (0: tiles without halo)
 };
 
-// Tiles with a halo (FP32C, the short-line batch instance: Voigt profile,
-// fixed cut of 2W + 1 < 1024 bins, no plinth): a tile of `tile_bins` bins owns
+// Tiles with a halo (FP32C, the short-line batch instances: Voigt profile,
+// fixed cut of 2W + 1 < 1024 bins, with or without the plinth): a tile of `tile_bins` bins owns
 // the lines whose nearest bin lies in its central tile_bins - 2H bins, and
 // its window reaches H bins further on each side, H a multiple of 32 with
 // H >= W + 2 -- every line is summed in one tile, unclipped.  Returns H, or 0
 // when the cut is too wide to leave at least 256 central bins.
 __device__ __host__ __forceinline__ int halo_bins(const GridD &g, int tile_bins)
 {
-    if (g.cut_mode != kCutFixed || !(g.W > 0.0) || g.plinth || g.profile != kProfVoigt ||
+    if (g.cut_mode != kCutFixed || !(g.W > 0.0) || g.profile != kProfVoigt ||
         2.0 * g.W + 1.0 >= 1024.0)
         return 0;
     const int need = (int)g.W + 3;   // ceil(W) + 2, W not an integer or W + 1 + 2
