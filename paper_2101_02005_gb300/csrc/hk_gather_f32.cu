@@ -527,6 +527,32 @@ __device__ __forceinline__ float r2_bound(float kmax, float b, float Y)
     return fmaf(xm, xm, Y);
 }
 
+// A wide line's batch flags for the tile [tg0, tg1], taken per line (one lane
+// per line, in the record stage) instead of per batch: bits 0-1 the rule that
+// serves the whole tile clear of the line's edge groups (1 one node, where the
+// tile lies in the one-node band; 2 two nodes, where it lies in the one- and
+// two-node bands and meets no four-node or core group; 0 neither); bit 2 set when every r2 of the tile stays below the
+// shared-reciprocal bound of that band; bit 3 set when x may be formed from the
+// tile's origin (one node, every |x| of the tile <= 4110: the origin's
+// rounding, at most half an ulp of 4110, moves r2 = x^2 + y^2 >= 1.5e6 by at
+// most 2 |x| 2.4e-4 / r2 <= 3e-7 relative).
+__device__ __forceinline__ int wide_flags(const Rec &q, int tg0, int tg1)
+{
+    int cls = 0;
+    const float km = (float)max(abs(32 * tg0 - q.c), abs(32 * tg1 + 31 - q.c));
+    if (tg0 > q.gA && tg1 < q.gB) {
+        if (tg1 < q.L2 || tg0 > q.R2) cls = 1;
+        // the two-node band, possibly reaching into the one-node band (the
+        // two-node rule is the more accurate one there), while X'^2 ~ r2^2
+        // stays in the float range
+        else if ((tg1 < q.L4 || tg0 > q.R4) && r2_bound(km, q.b, q.Y) < 1e17f) cls = 2;
+    }
+    if (cls == 0) return 0;
+    const bool share = r2_bound(km, q.b, q.Y) < (cls == 1 ? 1e17f : kShareR2);
+    const bool origin = cls == 1 && share && (km + 0.5f) * q.b < 1225.0f * 2e-7f * 16777216.0f;
+    return cls | (share ? 4 : 0) | (origin ? 8 : 0);
+}
+
 // The i-th 16-byte quad of a record, as one 128-bit shared load.
 __device__ __forceinline__ float4 quadf(const Rec &q, int i)
 {
@@ -734,24 +760,23 @@ __device__ __forceinline__ void core_quads(Smem &S, int warp, int lane, unsigned
 // tile far from all of them lies, for every line, inside one band clear of
 // the line's edge groups: then the warp sums the NLB lines per group in a
 // register (x from each line's exact integer bin offset, kept exact as a
-// float), one-node or two-node rule, less the lines' plinths.  Any other
-// (batch, tile) takes the per-line path.
+// float), one-node or two-node rule, less the lines' plinths.  A tile across
+// a line's one-/two-node boundary takes the two-node rule for every line.
+// Any other (batch, tile) takes the per-line path.
 template <int V>
 __device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0, int tg1,
                                               float *base, int lane, unsigned *queue, int &qn,
                                               int t0)
 {
     const Rec *R = &S.rec[warp][j0];
-    int cls = 0;   // 1: one-node rule over the whole tile for every line, 2: two-node
+    // the lines' flags for this tile (wide_flags): the common band, and whether
+    // every line may share reciprocals and form x from the tile's origin
+    int fand = 15, cls = -1;
 #pragma unroll
     for (int j = 0; j < NLB; ++j) {
-        const Rec &q = R[j];
-        int c = 0;
-        if (tg0 > q.gA && tg1 < q.gB) {
-            if (tg1 < q.L2 || tg0 > q.R2) c = 1;
-            else if (tg0 >= q.L2 && tg1 <= q.R2 && (tg1 < q.L4 || tg0 > q.R4)) c = 2;
-        }
-        cls = j == 0 ? c : (cls == c ? cls : 0);
+        const int f = __float_as_int(R[j].pad);
+        fand &= f;
+        cls = j == 0 ? (f & 3) : (cls == (f & 3) ? cls : 0);
     }
     if (cls == 0) {   // warp-uniform
         for (int j = 0; j < NLB; ++j) {
@@ -775,25 +800,12 @@ __device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0
     }
     // pairs of lines share a reciprocal when every r2 of the tile stays below
     // kShareR2 (one-node: 1/r2 products below 1e17^2 are safe as well)
-    bool share = true;
-#pragma unroll
-    for (int j = 0; j < NLB; ++j) {
-        const float km = (float)max(abs(32 * tg0 - R[j].c), abs(32 * tg1 + 31 - R[j].c));
-        share = share && r2_bound(km, b[j], R[j].Y) < (cls == 1 ? 1e17f : kShareR2);
-    }
+    const bool share = (fand & 4) != 0;
     float *p = base;
     float *const pe = base + 32 * (tg1 - tg0);
     // one node, with x from the tile's origin: x = fma(g, 32 b, x0), g the
-    // group count from the tile start.  In a one-node tile every |x| >= 1225
-    // (r2 >= 1.5e6), so the rounding of x0 costs at most ulp(|x0| + 1024 b)/1225
-    // relative in x: taken while that stays below 2e-7, else the exact offsets
-    bool origin = cls == 1 && share;
-#pragma unroll
-    for (int j = 0; j < NLB; ++j) {
-        const float xmax = fabsf(fmaf(kf[j], b[j], nrb[j])) + (float)(32 * (tg1 - tg0 + 1)) * b[j];
-        origin = origin && xmax < 1225.0f * 2e-7f * 16777216.0f;   // half an ulp <= xmax 2^-24
-    }
-    if (origin) {
+    // group count from the tile start (wide_flags bounds the cost of rounding x0)
+    if (fand & 8) {
         float x0[NLB], b32[NLB];
 #pragma unroll
         for (int j = 0; j < NLB; ++j) {
@@ -932,11 +944,13 @@ __global__ void __launch_bounds__(NT, 3)
             Rec q;
             if (l < l_end) {
                 make_rec(pr, g, l, scale, &q);
+                if (V & kVPeel) q.pad = __int_as_float(wide_flags(q, tg0, tg1));
             } else {  // past the item's lines: an empty record
                 q.lo = 0x3fffffff;
                 q.hi = -0x3fffffff;
                 q.gA = 1;
                 q.gB = 0;
+                q.pad = 0.0f;
             }
             S.rec[warp][lane] = q;
             __syncwarp();
