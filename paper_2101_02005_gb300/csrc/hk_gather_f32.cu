@@ -408,13 +408,14 @@ __device__ __forceinline__ void drain_rest(unsigned *queue, int &qn, Smem &S, in
     __syncwarp();
 }
 
-// All of one line's bins inside the tile (groups [tg0, tg1]).
+// One line's bins in groups [r0, r1] of the tile (groups [tg0, tg1]; base is
+// the warp's copy of the tile at its first group).
 template <int V>
 __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1, float *base,
                                         int lane, unsigned *queue, int &qn, Smem &S, int warp,
-                                        int t0)
+                                        int t0, int r0, int r1)
 {
-    const int ga = max(q.gA, tg0), gb = min(q.gB, tg1);
+    const int ga = max(q.gA, r0), gb = min(q.gB, r1);
     if (ga > gb) return;  // warp-uniform
     const int kfc = lane - q.c;
     if (V & kVDoppler) {
@@ -425,12 +426,12 @@ __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1
         sweep_binned<V>(q, q.gA, q.gB, ga, gb, tg0, base, kfc, lane);
         return;
     }
-    // a tile inside one one-node segment of a wide line, clear of its edge
+    // a range inside one one-node segment of a wide line, clear of its edge
     // groups: one unmasked pass and none of the other bands' prologues
-    if ((V & kVPeel) && tg1 < q.gB && ((tg0 > q.gA && tg1 < q.L2) || tg0 > q.R2)) {
-        float kf = (float)(32 * tg0 + kfc);
-        float *p = base;
-        float *const pe = base + 32 * (tg1 - tg0);
+    if ((V & kVPeel) && r1 < q.gB && ((r0 > q.gA && r1 < q.L2) || r0 > q.R2)) {
+        float kf = (float)(32 * r0 + kfc);
+        float *p = base + 32 * (r0 - tg0);
+        float *const pe = base + 32 * (r1 - tg0);
         for (; p < pe; p += 64, kf += 64.0f) {
             const float v0 = pair_f<kBandGH1, V>(q, kf);
             const float v1 = pair_f<kBandGH1, V>(q, kf + 32.0f);
@@ -521,6 +522,7 @@ __device__ __forceinline__ float gh2_pair_acc(float kf0, float b0, float nrb0, f
 // below kShareR2 both the denominators' product and the numerators' products
 // stay far inside the float range.
 constexpr float kShareR2 = 2.5e8f;
+constexpr int kMaskSpan = 4;      // widest masked spans of a wide batch (groups, both ends)
 __device__ __forceinline__ float r2_bound(float kmax, float b, float Y)
 {
     const float xm = (kmax + 0.5f) * b;
@@ -535,22 +537,29 @@ __device__ __forceinline__ float r2_bound(float kmax, float b, float Y)
 // shared-reciprocal bound of that band; bit 3 set when x may be formed from the
 // tile's origin (one node, every |x| of the tile <= 4110: the origin's
 // rounding, at most half an ulp of 4110, moves r2 = x^2 + y^2 >= 1.5e6 by at
-// most 2 |x| 2.4e-4 / r2 <= 3e-7 relative).
-__device__ __forceinline__ int wide_flags(const Rec &q, int tg0, int tg1)
+// most 2 |x| 2.4e-4 / r2 <= 3e-7 relative); bit 4 set when the two-node rule
+// may serve the line over the tile (r2 < 1e17), bit 5 when two-node values may
+// share reciprocals over the tile, bit 6 when the line's four-node and core
+// groups meet the tile.
+__device__ __forceinline__ int wide_flags(const Rec &q, int tg0, int tg1, bool voigt)
 {
-    int cls = 0;
     const float km = (float)max(abs(32 * tg0 - q.c), abs(32 * tg1 + 31 - q.c));
+    const float r2m = r2_bound(km, q.b, q.Y);
+    // the two-node rule may serve a Voigt line anywhere in the tile outside its
+    // four-node and core groups while X'^2 ~ r2^2 stays in the float range (it
+    // is the more accurate rule in the one-node band); the Lorentzian is the
+    // one-node rule itself
+    const bool gh2ok = voigt && r2m < 1e17f;
+    const bool meets4 = q.L4 <= q.R4 && q.L4 <= tg1 && q.R4 >= tg0;
+    int cls = 0;
     if (tg0 > q.gA && tg1 < q.gB) {
         if (tg1 < q.L2 || tg0 > q.R2) cls = 1;
-        // the two-node band, possibly reaching into the one-node band (the
-        // two-node rule is the more accurate one there), while X'^2 ~ r2^2
-        // stays in the float range
-        else if ((tg1 < q.L4 || tg0 > q.R4) && r2_bound(km, q.b, q.Y) < 1e17f) cls = 2;
+        else if (!meets4 && gh2ok) cls = 2;
     }
-    if (cls == 0) return 0;
-    const bool share = r2_bound(km, q.b, q.Y) < (cls == 1 ? 1e17f : kShareR2);
+    const bool share = cls != 0 && r2m < (cls == 1 ? 1e17f : kShareR2);
     const bool origin = cls == 1 && share && (km + 0.5f) * q.b < 1225.0f * 2e-7f * 16777216.0f;
-    return cls | (share ? 4 : 0) | (origin ? 8 : 0);
+    return cls | (share ? 4 : 0) | (origin ? 8 : 0) | (gh2ok ? 16 : 0) |
+           (gh2ok && r2m < kShareR2 ? 32 : 0) | (meets4 ? 64 : 0);
 }
 
 // The i-th 16-byte quad of a record, as one 128-bit shared load.
@@ -593,7 +602,7 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
     if (!uni) {   // warp-uniform
         for (int j = 0; j < NLB; ++j) {
             const Rec q = S.rec[warp][j0 + j];
-            do_line<V>(q, j0 + j, tg0, tg1, base, lane, queue, qn, S, warp, t0);
+            do_line<V>(q, j0 + j, tg0, tg1, base, lane, queue, qn, S, warp, t0, tg0, tg1);
         }
         return 0u;
     }
@@ -755,41 +764,21 @@ __device__ __forceinline__ void core_quads(Smem &S, int warp, int lane, unsigned
     __syncwarp();
 }
 
-// Batches of wide lines (the peeled instances: Voigt and Lorentzian, with or
-// without the plinth).  The lines of a batch have their own centres, but a
-// tile far from all of them lies, for every line, inside one band clear of
-// the line's edge groups: then the warp sums the NLB lines per group in a
-// register (x from each line's exact integer bin offset, kept exact as a
-// float), one-node or two-node rule, less the lines' plinths.  A tile across
-// a line's one-/two-node boundary takes the two-node rule for every line.
-// Any other (batch, tile) takes the per-line path.
+// One batched run over groups [g0, g1] (p: the warp's tile copy at g0) where
+// every line is inside its cut and served by rule `cls` (1: one node, 2: two
+// nodes): the warp sums the NLB lines per group in a register (x from each
+// line's exact integer bin offset, kept exact as a float), less the lines'
+// plinths.  share: pairs of lines share one reciprocal (every r2 of the run
+// below the rule's bound); origin: one node with x from the run's origin.
 template <int V>
-__device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0, int tg1,
-                                              float *base, int lane, unsigned *queue, int &qn,
-                                              int t0)
+__device__ __forceinline__ void wide_sweep(const Rec *R, int cls, bool share, bool origin, int g0,
+                                           int g1, float *p, int lane)
 {
-    const Rec *R = &S.rec[warp][j0];
-    // the lines' flags for this tile (wide_flags): the common band, and whether
-    // every line may share reciprocals and form x from the tile's origin
-    int fand = 15, cls = -1;
-#pragma unroll
-    for (int j = 0; j < NLB; ++j) {
-        const int f = __float_as_int(R[j].pad);
-        fand &= f;
-        cls = j == 0 ? (f & 3) : (cls == (f & 3) ? cls : 0);
-    }
-    if (cls == 0) {   // warp-uniform
-        for (int j = 0; j < NLB; ++j) {
-            const Rec q = S.rec[warp][j0 + j];
-            do_line<V>(q, j0 + j, tg0, tg1, base, lane, queue, qn, S, warp, t0);
-        }
-        return;
-    }
     float kf[NLB], b[NLB], nrb[NLB], P1[NLB], P2[NLB], sy[NLB];
     float H = 0.0f;
 #pragma unroll
     for (int j = 0; j < NLB; ++j) {
-        kf[j] = (float)(32 * tg0 + lane - R[j].c);   // exact: |offset| < 2^24 bins
+        kf[j] = (float)(32 * g0 + lane - R[j].c);   // exact: |offset| < 2^24 bins
         b[j] = R[j].b;
         nrb[j] = -R[j].rnb;
         sy[j] = R[j].sy;
@@ -798,14 +787,10 @@ __device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0
         P2[j] = 2.0f * Y;
         if (V & kVPlinth) H += R[j].h;
     }
-    // pairs of lines share a reciprocal when every r2 of the tile stays below
-    // kShareR2 (one-node: 1/r2 products below 1e17^2 are safe as well)
-    const bool share = (fand & 4) != 0;
-    float *p = base;
-    float *const pe = base + 32 * (tg1 - tg0);
-    // one node, with x from the tile's origin: x = fma(g, 32 b, x0), g the
-    // group count from the tile start (wide_flags bounds the cost of rounding x0)
-    if (fand & 8) {
+    float *const pe = p + 32 * (g1 - g0);
+    // one node, with x from the run's origin: x = fma(g, 32 b, x0), g the
+    // group count from the run's start (wide_flags bounds the cost of rounding x0)
+    if (origin) {
         float x0[NLB], b32[NLB];
 #pragma unroll
         for (int j = 0; j < NLB; ++j) {
@@ -868,6 +853,103 @@ __device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0
                 kf[j] += 32.0f;
             }
             p[0] += v;
+        }
+    }
+}
+
+
+// The two-node rule over groups [g0, g1] (p: the warp's tile copy at g0) where
+// lines of the batch start or end: each line adds where its lane's bin lies in
+// its cut, less its plinth there.
+template <int V>
+__device__ __forceinline__ void wide_masked(const Rec *R, int g0, int g1, float *p, int lane)
+{
+    float kf[NLB], b[NLB], nrb[NLB], Ym[NLB], Y2[NLB], sy[NLB];
+    int lo[NLB];
+    unsigned span[NLB];
+#pragma unroll
+    for (int j = 0; j < NLB; ++j) {
+        kf[j] = (float)(32 * g0 + lane - R[j].c);
+        b[j] = R[j].b;
+        nrb[j] = -R[j].rnb;
+        sy[j] = R[j].sy;
+        Ym[j] = R[j].Y - 0.5f;
+        Y2[j] = 2.0f * R[j].Y;
+        lo[j] = R[j].lo;
+        span[j] = (unsigned)(R[j].hi - R[j].lo);
+    }
+    int bin = 32 * g0 + lane;
+    float *const pe = p + 32 * (g1 - g0);
+    for (; p <= pe; p += 32, bin += 32) {
+        float v = 0.0f;
+#pragma unroll
+        for (int j = 0; j < NLB; ++j) {
+            float t = gh2_acc(kf[j], b[j], nrb[j], Ym[j], Y2[j], sy[j], 0.0f);
+            if (V & kVPlinth) t -= R[j].h;
+            v += (unsigned)(bin - lo[j]) <= span[j] ? t : 0.0f;
+            kf[j] += 32.0f;
+        }
+        p[0] += v;
+    }
+}
+
+// Batches of wide lines (the peeled instances: Voigt and Lorentzian, with or
+// without the plinth).  The lines of a batch have their own centres; their
+// per-tile flags (wide_flags) decide the tile's handling:
+// - every line in one band over the whole tile, clear of its edge groups: one
+//   batched run, one-node or two-node rule (a tile across a line's
+//   one-/two-node boundary takes the two-node rule for every line);
+// - else, when the two-node rule may serve every line over the tile and no
+//   line's four-node or core groups meet it: the spans where lines start or
+//   end ([min gA, max gA], [min gB, max gB]) run the masked two-node rule and
+//   the groups between them one unmasked batched two-node run;
+// - else the whole tile goes line by line.
+template <int V>
+__device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0, int tg1,
+                                              float *base, int lane, unsigned *queue, int &qn,
+                                              int t0)
+{
+    const Rec *R = &S.rec[warp][j0];
+    int fand = 127, fany = 0, cls = -1;
+    int A0 = INT_MAX, A1 = INT_MIN, B0 = INT_MAX, B1 = INT_MIN;
+#pragma unroll
+    for (int j = 0; j < NLB; ++j) {
+        const int f = __float_as_int(R[j].pad);
+        fand &= f;
+        fany |= f;
+        cls = j == 0 ? (f & 3) : (cls == (f & 3) ? cls : 0);
+        A0 = min(A0, R[j].gA);
+        A1 = max(A1, R[j].gA);
+        B0 = min(B0, R[j].gB);
+        B1 = max(B1, R[j].gB);
+    }
+    const bool edges = cls == 0;
+    // masked spans of at most kMaskSpan groups in all: the masked rule takes
+    // every line in every group of a span, whether the line has bins there or not
+    const int span = max(min(A1, tg1) - max(A0, tg0) + 1, 0) + max(min(B1, tg1) - max(B0, tg0) + 1, 0);
+    if (edges && !((fand & 16) && !(fany & 64) && A1 < B0 && span <= kMaskSpan)) {
+        for (int j = 0; j < NLB; ++j) {
+            const Rec q = S.rec[warp][j0 + j];
+            do_line<V>(q, j0 + j, tg0, tg1, base, lane, queue, qn, S, warp, t0, tg0, tg1);
+        }
+        return;
+    }
+    const int g0 = edges ? max(A1 + 1, tg0) : tg0, g1 = edges ? min(B0 - 1, tg1) : tg1;
+    if (g0 <= g1)
+        wide_sweep<V>(R, edges ? 2 : cls, (fand & (edges ? 32 : 4)) != 0, !edges && (fand & 8),
+                      g0, g1, base + 32 * (g0 - tg0), lane);
+    if (edges) {   // the masked spans, from the records again
+        int a0 = INT_MAX, a1 = INT_MIN, b0 = INT_MAX, b1 = INT_MIN;
+#pragma unroll
+        for (int j = 0; j < NLB; ++j) {
+            a0 = min(a0, R[j].gA);
+            a1 = max(a1, R[j].gA);
+            b0 = min(b0, R[j].gB);
+            b1 = max(b1, R[j].gB);
+        }
+        for (int k = 0; k < 2; ++k) {
+            const int m0 = max(k ? b0 : a0, tg0), m1 = min(k ? b1 : a1, tg1);
+            if (m0 <= m1) wide_masked<V>(R, m0, m1, base + 32 * (m0 - tg0), lane);
         }
     }
 }
@@ -944,7 +1026,8 @@ __global__ void __launch_bounds__(NT, 3)
             Rec q;
             if (l < l_end) {
                 make_rec(pr, g, l, scale, &q);
-                if (V & kVPeel) q.pad = __int_as_float(wide_flags(q, tg0, tg1));
+                if (V & kVPeel)
+                    q.pad = __int_as_float(wide_flags(q, tg0, tg1, g.profile == kProfVoigt));
             } else {  // past the item's lines: an empty record
                 q.lo = 0x3fffffff;
                 q.hi = -0x3fffffff;
@@ -969,7 +1052,7 @@ __global__ void __launch_bounds__(NT, 3)
                     // a register copy: the record must not be re-read from shared
                     // memory after every store into the tile copy
                     const Rec q = S.rec[warp][j];
-                    do_line<V>(q, j, tg0, tg1, accb, lane, queue, qn, S, warp, t0);
+                    do_line<V>(q, j, tg0, tg1, accb, lane, queue, qn, S, warp, t0, tg0, tg1);
                 }
             }
             drain_rest(queue, qn, S, warp, lane, t0, accb - lane);
