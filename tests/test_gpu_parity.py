@@ -701,3 +701,49 @@ def test_voigt_bands_per_pair_accuracy(hk, cut):
         assert rel.max() <= tol_max and np.median(rel) <= tol_med, (
             name, cut, float(rel.max()), float(np.median(rel)), int(np.flatnonzero(m)[i]))
     assert np.array_equal(ref == 0, out32.cpu().numpy() == 0)
+
+
+def test_dense_wide_lines(hk):
+    """Dense wide lines (cut 25 at 0.01 cm^-1: 5001 bins, the peeled instance)
+    in clusters, so that batches of lines dealt 8 apart still lie within a
+    few groups of each other: tiles in one band for every line (one-node
+    runs from the tile origin, shared reciprocals), tiles across lines'
+    one-/two-node boundaries (the two-node rule for every line), tiles where
+    lines start or end (masked two-node spans), tiles with lines' four-node
+    and core groups (line by line), and lines with y >> 50 (no four-node
+    band).  Voigt and Lorentzian, with and without the plinth, at two (T, P)
+    points; FP32C against the oracle over the whole array."""
+    rng = np.random.default_rng(2102)
+    dnu, nbins = 0.01, 40000
+    centres = np.sort(rng.uniform(30.0, 370.0, 60))
+    nu0 = np.sort(np.concatenate([c + rng.uniform(-0.05, 0.05, int(rng.integers(20, 80)))
+                                  for c in centres]))
+    n = nu0.size
+    gam = rng.uniform(0.01, 0.1, n).astype(np.float32)
+    gam[rng.uniform(size=n) < 0.05] = 40.0
+    L = synth.LineList(nu0, (10 ** rng.uniform(-24, -20, n)).astype(np.float32),
+                       rng.exponential(1500.0, n).astype(np.float32), gam,
+                       rng.uniform(0.3, 0.8, n).astype(np.float32), 18.0)
+    grid = synth.Grid(0.0, dnu, nbins)
+    D = hk.DeviceLines.from_host(L)
+    g = hk.make_grid(*grid.astuple())
+    V, LZ = hk.HK_PROFILE_VOIGT, hk.HK_PROFILE_LORENTZ
+    for T, P in [(1000.0, 1.0), (300.0, 20.0)]:
+        st = hk.make_state(T, P, float(Q(T)))
+        args = (L.as_oracle(), grid.astuple(), (T, P, float(Q(T)), QREF), 25.0)
+        base = {}
+        for prof in (V, LZ):
+            for plinth in (False, True):
+                flags = (hk.HK_REMOVE_PLINTH if plinth else 0) | hk.HK_SIGMA_F64
+                opts = hk.make_opts(QREF, 25.0, hk.HK_FP32C, flags=flags, profile=prof)
+                got = hk.hk_cross_section(D, g, st, opts)
+                hk.hk_sync_status()
+                got = got.cpu().numpy()
+                ref = oracle.cross_section(*args, plinth=plinth, profile=prof)
+                what = f"dense wide profile={prof} plinth={plinth} T={T} P={P}"
+                assert np.all(got[ref == 0] == 0), what
+                if not plinth:
+                    base[prof] = ref
+                    record(what, assert_sigma_close(got, ref, what))
+                else:
+                    record(what, assert_plinth_close(got, ref, base[prof], what))
