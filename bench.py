@@ -156,11 +156,11 @@ def smi_gpu_id(dev):
 
 def measure_peaks(hk, dev, ms=1000.0):
     """Measured pipe throughputs of this GPU (hk_measure_peak), each with the
-    SM clock sampled while it ran: FP32 FMA, MUFU reciprocal and exp2, FP64
-    FMA (lane operations per second)."""
+    SM clock sampled while it ran: FP32 FMA (scalar, and packed FP32x2), MUFU
+    reciprocal and exp2, FP64 FMA (lane operations per second)."""
     out = {}
-    for kind, name in [(hk.PEAK_FFMA, "ffma"), (hk.PEAK_RCP, "mufu_rcp"), (hk.PEAK_EX2, "mufu_ex2"),
-                       (hk.PEAK_DFMA, "dfma")]:
+    for kind, name in [(hk.PEAK_FFMA, "ffma"), (hk.PEAK_FFMA2, "ffma2"), (hk.PEAK_RCP, "mufu_rcp"),
+                       (hk.PEAK_EX2, "mufu_ex2"), (hk.PEAK_DFMA, "dfma")]:
         hk.hk_measure_peak(kind, 100.0)
         s = ClockSampler(smi_gpu_id(dev))
         s.start()

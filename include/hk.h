@@ -363,7 +363,9 @@ int hk_profile(int mode, double *ms, int64_t *launches);
  * one pipe of the current device, for the rooflines of the kernels.  kind 0:
  * FP32 fused multiply-adds per second; 1: MUFU reciprocals (rcp.approx.ftz)
  * per second; 2: MUFU base-2 exponentials (ex2.approx.ftz) per second; 3: FP64
- * fused multiply-adds per second.  Every SM runs 64 warps of independent
+ * fused multiply-adds per second; 4: FP32 fused multiply-adds per second
+ * issued as packed FP32x2 instructions (two per lane and instruction).
+ * Every SM runs 64 warps of independent
  * chains of the operation; a calibration launch sizes launches of ~100 ms,
  * repeated for about target_ms (0 < target_ms <= 60000).  *ops_per_s: HOST
  * double.  Synchronises `stream`; uses the scratch pool (2.5 MB). */

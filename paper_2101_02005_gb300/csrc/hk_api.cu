@@ -1050,7 +1050,7 @@ int hk_autotune(const hk_lines *lines, const hk_grid *grid, const hk_state *stat
 
 int hk_measure_peak(int kind, double target_ms, double *ops_per_s, void *stream)
 {
-    if (kind < 0 || kind > 3 || !ops_per_s || !(target_ms > 0.0) || target_ms > 60000.0)
+    if (kind < 0 || kind > 4 || !ops_per_s || !(target_ms > 0.0) || target_ms > 60000.0)
         return HK_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     const int sms = num_sms();

@@ -599,6 +599,12 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
     }
     const bool central = mL4 <= MR4;
     uni = uni && (!central || (mL4 > gA && MR4 < gB));
+    // the lines' cut ranges: most batches share one (the same centre bin and
+    // nearly the same remainder), and then an edge group needs one mask
+    const int lo0 = st[0].w, hi0 = rg[0].x;
+    bool same_cut = true;
+#pragma unroll
+    for (int j = 1; j < NLB; ++j) same_cut = same_cut && st[j].w == lo0 && rg[j].x == hi0;
     if (!uni) {   // warp-uniform
         for (int j = 0; j < NLB; ++j) {
             const Rec q = S.rec[warp][j0 + j];
@@ -625,6 +631,13 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
 #pragma unroll
         for (int j = 0; j < NLB; ++j) H += R[j].h;
     }
+    // the batch's two-node sum at one group, less the plinths
+    auto two_node = [&](float kf) {
+        float v = -H;
+#pragma unroll
+        for (int j = 0; j < NLB; ++j) v = gh2_acc(kf, b[j], nrb[j], Ym[j], Y2[j], sy[j], v);
+        return v;
+    };
     // the two-node rule over [g0, g1] (clipped to the tile), unmasked
     auto interior = [&](int g0, int g1) {
         g0 = max(g0, tg0);
@@ -633,25 +646,25 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
         float kf = (float)(32 * g0 + kfc);
         float *p = base + 32 * (g0 - tg0);
         float *const pe = base + 32 * (g1 - tg0);
-        for (; p <= pe; p += 32, kf += 32.0f) {
-            float v0 = -H;
-#pragma unroll
-            for (int j = 0; j < NLB; ++j)
-                v0 = gh2_acc(kf, b[j], nrb[j], Ym[j], Y2[j], sy[j], v0);
-            p[0] += v0;
-        }
+        for (; p <= pe; p += 32, kf += 32.0f) p[0] += two_node(kf);
     };
     // an edge group: each line adds where its lane's bin is inside its range
+    // (one mask for the batch when the lines share their range)
     auto edge = [&](int g) {
         if (g < tg0 || g > tg1) return;
         const float kf = (float)(32 * g + kfc);
         const int bin = 32 * g + lane;
-        float v = 0.0f;
+        float v;
+        if (same_cut) {   // warp-uniform
+            v = (unsigned)(bin - lo0) <= (unsigned)(hi0 - lo0) ? two_node(kf) : 0.0f;
+        } else {
+            v = 0.0f;
 #pragma unroll
-        for (int j = 0; j < NLB; ++j) {
-            float t = gh2_acc(kf, b[j], nrb[j], Ym[j], Y2[j], sy[j], 0.0f);
-            if (V & kVPlinth) t -= R[j].h;
-            v += (bin >= R[j].lo && bin <= R[j].hi) ? t : 0.0f;
+            for (int j = 0; j < NLB; ++j) {
+                float t = gh2_acc(kf, b[j], nrb[j], Ym[j], Y2[j], sy[j], 0.0f);
+                if (V & kVPlinth) t -= R[j].h;
+                v += (bin >= R[j].lo && bin <= R[j].hi) ? t : 0.0f;
+            }
         }
         base[32 * (g - tg0)] += v;
     };
@@ -665,41 +678,57 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
     interior(gA + 1, mL4 - 1);
     interior(MR4 + 1, gB - 1);
     // the central groups: the four-node rule (valid for every r2 >= 64) for
-    // every bin but each line's core bins, summed over the batch; the core
-    // bins go to the caller's core-range pass.  The two-node parameters are
-    // dead here, which keeps the registers in bounds.
+    // every bin outside the batch's core bins U, summed over the batch; U is
+    // the union of the lines' core ranges (r2 < 64), and the caller's core
+    // pass evaluates every line at every bin of U with the trapezoid rule.
+    // The two-node parameters are dead here, which keeps the registers in
+    // bounds.
     const int c0g = max(mL4, tg0), c1g = min(MR4, tg1);
     if (c0g > c1g) return 0xfu;
+    int ulo = INT_MAX, uhi = INT_MIN;
+#pragma unroll
+    for (int j = 0; j < NLB; ++j) {
+        const int cl = quadi(R[j], 3).w, ch = quadi(R[j], 4).x;
+        if (cl <= ch) {
+            ulo = min(ulo, cl);
+            uhi = max(uhi, ch);
+        }
+    }
+    if (ulo > uhi) {   // no core bins: a U no bin can meet
+        ulo = 0x3fffffff;
+        uhi = ulo;
+    }
+    const unsigned uspan = (unsigned)(uhi - ulo);
     // (the four-node constants are read from shared memory in the loop: a
     // 128-bit load per line and group costs less than holding them)
     float kf = (float)(32 * c0g + kfc);
     float *p = base + 32 * (c0g - tg0);
-    for (int g = c0g; g <= c1g; ++g, kf += 32.0f, p += 32) {
-        const int bin = 32 * g + lane;
-        float v = 0.0f;
+    int bin = 32 * c0g + lane;
+    for (int g = c0g; g <= c1g; ++g, kf += 32.0f, p += 32, bin += 32) {
+        float v = -H;
 #pragma unroll
         for (int j = 0; j < NLB; ++j) {
             const float4 f = quadf(R[j], 1);   // (Ca, Cb, sa, sb)
-            const int cl = quadi(R[j], 3).w, ch = quadi(R[j], 4).x;
             float r2;
-            float t = gh4_val(kf, b[j], nrb[j], quadf(R[j], 0).z, f.x, f.y, f.z, f.w, &r2);
-            if (V & kVPlinth) t -= R[j].h;   // (the core bins subtract it in the core pass)
-            v += (bin >= cl && bin <= ch) ? 0.0f : t;
+            v += gh4_val(kf, b[j], nrb[j], quadf(R[j], 0).z, f.x, f.y, f.z, f.w, &r2);
         }
-        p[0] += v;
+        if ((unsigned)(bin - ulo) > uspan) p[0] += v;
     }
     return 0xfu;
 }
 
-// The core bins (r2 < 64) of the batches whose lines took the batched sweep
-// (`mask`: 4 bits per batch).  Each line's core bins are a contiguous range
-// (Rec::cl .. ch) and the 4 lines of a batch share their centre bin, so a
-// batch's core pairs lie in one short union range U of bins.  The pairs of
-// all such batches are laid end to end as (batch, bin u in U, line) with the
-// line innermost -- 4 slots per bin, so the lanes of an aligned quad hold one
-// bin's 4 values, summed by two shuffles and added by one lane -- and
-// evaluated 32 slots at a time.  A slot whose line has no core pair at u adds
-// 0.  Quads of two batches in one step may share a bin: the update is a
+// The core bins of the batches whose lines took the batched sweep (`mask`: 4
+// bits per batch).  Each line's core bins (r2 < 64) are a contiguous range
+// (Rec::cl .. ch) and the 4 lines of a batch share their centre bin, so they
+// lie in one short union range U of bins, which the batched sweep left out
+// for all 4 lines.  Here every line takes every bin of U inside its cut with
+// the trapezoid rule (valid for any r2; a bin of U outside a line's own core
+// range is one it would otherwise have taken with the four-node rule).  The
+// pairs of all such batches are laid end to end as (batch, bin u in U, line)
+// with the line innermost -- 4 slots per bin, so the lanes of an aligned quad
+// hold one bin's 4 values, summed by two shuffles and added by one lane --
+// and evaluated 32 slots at a time.  A slot whose bin lies outside its line's
+// cut adds 0.  Quads of two batches in one step may share a bin: the update is a
 // shared-memory atomic add.  The warp's queue rows serve as scratch (the
 // queue is empty here).
 __device__ __forceinline__ void core_quads(Smem &S, int warp, int lane, unsigned mask, int t0,
@@ -751,7 +780,7 @@ __device__ __forceinline__ void core_quads(Smem &S, int warp, int lane, unsigned
         const int u = ub[k] + (rel >> 2);
         const Rec &q = S.rec[warp][4 * k + (rel & 3)];
         float v = 0.0f;
-        if (sl < total && u >= quadi(q, 3).w && u <= quadi(q, 4).x) {
+        if (sl < total && u >= quadi(q, 2).w && u <= quadi(q, 3).x) {
             const float4 p0 = quadf(q, 0);   // (b, rn b, Y, sy)
             const float4 p5 = quadf(q, 5);   // (R2, rn, s, y)
             const float kk = (float)(u - quadi(q, 2).x);

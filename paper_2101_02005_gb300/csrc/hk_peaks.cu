@@ -1,5 +1,6 @@
 // hk_peaks.cu -- throughput microbenchmarks of the pipes the Voigt kernels
-// run on (FP32 FMA, the MUFU reciprocal and exp2, FP64 FMA), so that their
+// run on (FP32 FMA, scalar and packed FP32x2, the MUFU reciprocal and exp2,
+// FP64 FMA), so that their
 // rooflines are stated against measured peaks of this GPU rather than
 // nominal unit counts.
 //
@@ -64,6 +65,28 @@ template <int KIND> __global__ void __launch_bounds__(NT) k_peak_f32(float *out,
     if (s == -12345.678f) out[blockIdx.x * NT + threadIdx.x] = s;
 }
 
+// Packed FP32x2 FMA (sm_100 and later: one instruction, two FMAs per lane):
+// a = a m + c on both halves of NCH register pairs.
+__global__ void __launch_bounds__(NT) k_peak_f32x2(float *out, int iters, float seed)
+{
+    float2 a[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c)
+        a[c] = make_float2(seed + 0.01f * (float)(threadIdx.x + c), seed - 0.01f * (float)c);
+    const float2 m = make_float2(0.9999f, 0.9998f), k = make_float2(1e-5f, 2e-5f);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+#pragma unroll
+            for (int c = 0; c < NCH; ++c) a[c] = __ffma2_rn(a[c], m, k);
+        }
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) s += a[c].x + a[c].y;
+    if (s == -12345.678f) out[blockIdx.x * NT + threadIdx.x] = s;
+}
+
 __global__ void __launch_bounds__(NT) k_peak_f64(double *out, int iters, double seed)
 {
     double a[NCH];
@@ -103,6 +126,10 @@ int peak_launch(int kind, int iters, int num_sms, void *scratch, double *ops, cu
         break;
     case 3:
         peaks::k_peak_f64<<<blocks, peaks::NT, 0, st>>>((double *)scratch, iters, 0.5);
+        break;
+    case 4:   // two FMAs per lane and instruction
+        *ops *= 2.0;
+        peaks::k_peak_f32x2<<<blocks, peaks::NT, 0, st>>>((float *)scratch, iters, 0.5f);
         break;
     default:
         return HK_EINVAL;

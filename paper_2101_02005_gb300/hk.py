@@ -389,12 +389,13 @@ def hk_profile(mode: int):
     return ms.value, int(n.value)
 
 
-PEAK_FFMA, PEAK_RCP, PEAK_EX2, PEAK_DFMA = 0, 1, 2, 3
+PEAK_FFMA, PEAK_RCP, PEAK_EX2, PEAK_DFMA, PEAK_FFMA2 = 0, 1, 2, 3, 4
 
 
 def hk_measure_peak(kind: int, target_ms: float = 1000.0, stream=None) -> float:
     """Measured operations per second of one pipe (instrumentation):
-    PEAK_FFMA (FMAs), PEAK_RCP, PEAK_EX2 (MUFU ops), PEAK_DFMA (FP64 FMAs)."""
+    PEAK_FFMA (FMAs), PEAK_RCP, PEAK_EX2 (MUFU ops), PEAK_DFMA (FP64 FMAs), PEAK_FFMA2 (FMAs
+    issued as packed FP32x2 instructions)."""
     v = ctypes.c_double(0.0)
     _check("hk_measure_peak", lib().hk_measure_peak(int(kind), float(target_ms), ctypes.byref(v),
                                                     _stream(stream)))
