@@ -474,7 +474,8 @@ __device__ __forceinline__ void do_line(const Rec &q, int slot, int tg0, int tg1
 // two-node rule is the same rational function, regrouped in X = x^2).  A
 // batch whose lines differ in gA, gB or the nearest bin c, or whose central
 // groups reach gA or gB, takes the per-line path.
-constexpr int NLB = 4;
+constexpr int NLB = 4;   // lines per batch: wide lines
+constexpr int NLS = 4;   // lines per batch: short lines
 
 // Two-node value of a pair, as fma(num, 1/d, acc).  The rule's
 // |z^2 - 1/2|^2 = X^2 + (2Y - 1) X + (Y + 1/2)^2 (X = x^2) is, with
@@ -572,50 +573,74 @@ __device__ __forceinline__ int4 quadi(const Rec &q, int i)
     return reinterpret_cast<const int4 *>(&q)[i];
 }
 
+// The structure of each batch of NLS consecutive lines (lanes NLS k ..
+// NLS k + NLS - 1 of the record stage), taken lane-parallel by shuffles and
+// kept in the batch's first record, in fields the short-line path does not
+// otherwise read: Lc, Rc = the smallest L4 and the largest R4 of the lines
+// with a four-node band; L2, R2 = the union of the lines' core bin ranges
+// (empty: INT_MAX, INT_MIN); pad = flags, bit 0 when the lines share c, gA
+// and gB (gA <= gB), bit 1 when they share their cut range [lo, hi].
+__device__ __forceinline__ void batch_summary(Rec &q, int lane)
+{
+    constexpr unsigned FULL = 0xffffffffu, kAll = (1u << NLS) - 1u;
+    const int first = lane & ~(NLS - 1);
+    // every lane takes every shuffle (no short-circuit evaluation around them)
+    const int c0 = __shfl_sync(FULL, q.c, first), gA0 = __shfl_sync(FULL, q.gA, first),
+              gB0 = __shfl_sync(FULL, q.gB, first), lo0 = __shfl_sync(FULL, q.lo, first),
+              hi0 = __shfl_sync(FULL, q.hi, first);
+    const bool same = (c0 == q.c) & (gA0 == q.gA) & (gB0 == q.gB) & (q.gA <= q.gB);
+    const bool scut = (lo0 == q.lo) & (hi0 == q.hi);
+    const unsigned ms = __ballot_sync(FULL, same), mc = __ballot_sync(FULL, scut);
+    const bool has4 = q.L4 <= q.R4, hasc = q.cl <= q.ch;
+    int a = has4 ? q.L4 : INT_MAX, e = has4 ? q.R4 : INT_MIN;
+    int u = hasc ? q.cl : INT_MAX, v = hasc ? q.ch : INT_MIN;
+#pragma unroll
+    for (int o = 1; o < NLS; o <<= 1) {
+        a = min(a, __shfl_xor_sync(FULL, a, o));
+        e = max(e, __shfl_xor_sync(FULL, e, o));
+        u = min(u, __shfl_xor_sync(FULL, u, o));
+        v = max(v, __shfl_xor_sync(FULL, v, o));
+    }
+    if (lane == first) {
+        q.Lc = a;
+        q.Rc = e;
+        q.L2 = u;
+        q.R2 = v;
+        q.pad = __int_as_float((((ms >> first) & kAll) == kAll ? 1 : 0) |
+                               (((mc >> first) & kAll) == kAll ? 2 : 0));
+    }
+}
+
 // Returns the lines (bit j for line j0 + j) whose core bins are left to the
 // caller's core-range pass: those of a batch that took the batched sweep.
-template <int V>
+template <int V, int NB>
 __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0, int tg1,
                                              float *base, int lane, unsigned *queue, int &qn,
                                              int t0)
 {
+    constexpr unsigned kAll = (1u << NB) - 1u;
     const Rec *R = &S.rec[warp][j0];
-    int4 st[NLB], rg[NLB];     // (c, gA, gB, lo), (hi, L4, R4, cl)
-#pragma unroll
-    for (int j = 0; j < NLB; ++j) {
-        st[j] = quadi(R[j], 2);
-        rg[j] = quadi(R[j], 3);
-    }
-    const int c0 = st[0].x, gA = st[0].y, gB = st[0].z;
-    int mL4 = INT_MAX, MR4 = INT_MIN;
-    bool uni = gA <= gB;
-#pragma unroll
-    for (int j = 0; j < NLB; ++j) {
-        uni = uni && st[j].y == gA && st[j].z == gB && st[j].x == c0;
-        if (rg[j].y <= rg[j].z) {
-            mL4 = min(mL4, rg[j].y);
-            MR4 = max(MR4, rg[j].z);
-        }
-    }
+    // the batch's structure, from the summary in its first record
+    const int4 s0 = quadi(R[0], 2);   // (c, gA, gB, lo)
+    const int4 s4 = quadi(R[0], 4);   // (ch, smallest L4, largest R4, first bin of U)
+    const int c0 = s0.x, gA = s0.y, gB = s0.z, lo0 = s0.w, mL4 = s4.y, MR4 = s4.z;
+    const int flags = __float_as_int(R[0].pad);
     const bool central = mL4 <= MR4;
-    uni = uni && (!central || (mL4 > gA && MR4 < gB));
+    const bool uni = (flags & 1) && (!central || (mL4 > gA && MR4 < gB));
     // the lines' cut ranges: most batches share one (the same centre bin and
     // nearly the same remainder), and then an edge group needs one mask
-    const int lo0 = st[0].w, hi0 = rg[0].x;
-    bool same_cut = true;
-#pragma unroll
-    for (int j = 1; j < NLB; ++j) same_cut = same_cut && st[j].w == lo0 && rg[j].x == hi0;
+    const bool same_cut = (flags & 2) != 0;
     if (!uni) {   // warp-uniform
-        for (int j = 0; j < NLB; ++j) {
+        for (int j = 0; j < NB; ++j) {
             const Rec q = S.rec[warp][j0 + j];
             do_line<V>(q, j0 + j, tg0, tg1, base, lane, queue, qn, S, warp, t0, tg0, tg1);
         }
         return 0u;
     }
     if (max(gA, tg0) > min(gB, tg1)) return 0u;
-    float b[NLB], nrb[NLB], Ym[NLB], Y2[NLB], sy[NLB];
+    float b[NB], nrb[NB], Ym[NB], Y2[NB], sy[NB];
 #pragma unroll
-    for (int j = 0; j < NLB; ++j) {
+    for (int j = 0; j < NB; ++j) {
         const float4 t = quadf(R[j], 0);   // (b, rn b, Y, sy)
         b[j] = t.x;
         nrb[j] = -t.y;              // x = (k - rn) b, the per-line path's arithmetic
@@ -629,13 +654,13 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
     float H = 0.0f;
     if (V & kVPlinth) {
 #pragma unroll
-        for (int j = 0; j < NLB; ++j) H += R[j].h;
+        for (int j = 0; j < NB; ++j) H += R[j].h;
     }
     // the batch's two-node sum at one group, less the plinths
     auto two_node = [&](float kf) {
         float v = -H;
 #pragma unroll
-        for (int j = 0; j < NLB; ++j) v = gh2_acc(kf, b[j], nrb[j], Ym[j], Y2[j], sy[j], v);
+        for (int j = 0; j < NB; ++j) v = gh2_acc(kf, b[j], nrb[j], Ym[j], Y2[j], sy[j], v);
         return v;
     };
     // the two-node rule over [g0, g1] (clipped to the tile), unmasked
@@ -656,11 +681,11 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
         const int bin = 32 * g + lane;
         float v;
         if (same_cut) {   // warp-uniform
-            v = (unsigned)(bin - lo0) <= (unsigned)(hi0 - lo0) ? two_node(kf) : 0.0f;
+            v = (unsigned)(bin - lo0) <= (unsigned)(R[0].hi - lo0) ? two_node(kf) : 0.0f;
         } else {
             v = 0.0f;
 #pragma unroll
-            for (int j = 0; j < NLB; ++j) {
+            for (int j = 0; j < NB; ++j) {
                 float t = gh2_acc(kf, b[j], nrb[j], Ym[j], Y2[j], sy[j], 0.0f);
                 if (V & kVPlinth) t -= R[j].h;
                 v += (bin >= R[j].lo && bin <= R[j].hi) ? t : 0.0f;
@@ -669,11 +694,11 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
         base[32 * (g - tg0)] += v;
     };
     edge(gA);
-    if (gB == gA) return 0xfu;
+    if (gB == gA) return kAll;
     edge(gB);
     if (!central) {
         interior(gA + 1, gB - 1);
-        return 0xfu;
+        return kAll;
     }
     interior(gA + 1, mL4 - 1);
     interior(MR4 + 1, gB - 1);
@@ -684,16 +709,8 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
     // The two-node parameters are dead here, which keeps the registers in
     // bounds.
     const int c0g = max(mL4, tg0), c1g = min(MR4, tg1);
-    if (c0g > c1g) return 0xfu;
-    int ulo = INT_MAX, uhi = INT_MIN;
-#pragma unroll
-    for (int j = 0; j < NLB; ++j) {
-        const int cl = quadi(R[j], 3).w, ch = quadi(R[j], 4).x;
-        if (cl <= ch) {
-            ulo = min(ulo, cl);
-            uhi = max(uhi, ch);
-        }
-    }
+    if (c0g > c1g) return kAll;
+    int ulo = s4.w, uhi = R[0].R2;   // U (empty: ulo > uhi)
     if (ulo > uhi) {   // no core bins: a U no bin can meet
         ulo = 0x3fffffff;
         uhi = ulo;
@@ -707,14 +724,14 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
     for (int g = c0g; g <= c1g; ++g, kf += 32.0f, p += 32, bin += 32) {
         float v = -H;
 #pragma unroll
-        for (int j = 0; j < NLB; ++j) {
+        for (int j = 0; j < NB; ++j) {
             const float4 f = quadf(R[j], 1);   // (Ca, Cb, sa, sb)
             float r2;
             v += gh4_val(kf, b[j], nrb[j], quadf(R[j], 0).z, f.x, f.y, f.z, f.w, &r2);
         }
         if ((unsigned)(bin - ulo) > uspan) p[0] += v;
     }
-    return 0xfu;
+    return kAll;
 }
 
 // The core bins of the batches whose lines took the batched sweep (`mask`: 4
@@ -731,40 +748,34 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
 // cut adds 0.  Quads of two batches in one step may share a bin: the update is a
 // shared-memory atomic add.  The warp's queue rows serve as scratch (the
 // queue is empty here).
+template <int NB>
 __device__ __forceinline__ void core_quads(Smem &S, int warp, int lane, unsigned mask, int t0,
                                            int t1, float *accw)
 {
+    constexpr int NBR = 32 / NB;                      // batches per round
+    constexpr int LG = NB == 8 ? 3 : 2;               // log2 NB
+    constexpr unsigned kAll = (1u << NB) - 1u;
     int u0 = 0, nu = 0;
-    if (lane < 8 && ((mask >> (4 * lane)) & 0xfu) == 0xfu) {
-        int lo = INT_MAX, hi = INT_MIN;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const Rec &q = S.rec[warp][4 * lane + j];
-            const int cl = quadi(q, 3).w, ch = quadi(q, 4).x;
-            if (cl <= ch) {
-                lo = min(lo, cl);
-                hi = max(hi, ch);
-            }
-        }
-        lo = max(lo, t0);
-        hi = min(hi, t1);
+    if (lane < NBR && ((mask >> (NB * lane)) & kAll) == kAll) {
+        const Rec &q = S.rec[warp][NB * lane];     // the batch summary: U = [L2, R2]
+        const int lo = max(q.L2, t0), hi = min(q.R2, t1);
         if (lo <= hi) {
             u0 = lo;
             nu = hi - lo + 1;
         }
     }
-    int inc = 4 * nu;
+    int inc = NB * nu;
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
+    for (int o = 1; o < NBR; o <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += t;
     }
-    const int total = __shfl_sync(0xffffffffu, inc, 7);
+    const int total = __shfl_sync(0xffffffffu, inc, NBR - 1);
     if (total == 0) return;   // warp-uniform
     int *pre = reinterpret_cast<int *>(S.queue[warp]);   // first slot of batch k
-    int *ub = pre + 8;                                   // first bin of U of batch k
-    if (lane < 8) {
-        pre[lane] = inc - 4 * nu;
+    int *ub = pre + NBR;                                 // first bin of U of batch k
+    if (lane < NBR) {
+        pre[lane] = inc - NB * nu;
         ub[lane] = u0;
     }
     __syncwarp();
@@ -774,11 +785,11 @@ __device__ __forceinline__ void core_quads(Smem &S, int warp, int lane, unsigned
         // slots share their successor's first slot)
         int k = 0;
 #pragma unroll
-        for (int st = 4; st > 0; st >>= 1)
-            if (k + st < 8 && pre[k + st] <= sl) k += st;
+        for (int st = NBR / 2; st > 0; st >>= 1)
+            if (k + st < NBR && pre[k + st] <= sl) k += st;
         const int rel = sl - pre[k];
-        const int u = ub[k] + (rel >> 2);
-        const Rec &q = S.rec[warp][4 * k + (rel & 3)];
+        const int u = ub[k] + (rel >> LG);
+        const Rec &q = S.rec[warp][NB * k + (rel & (NB - 1))];
         float v = 0.0f;
         if (sl < total && u >= quadi(q, 2).w && u <= quadi(q, 3).x) {
             const float4 p0 = quadf(q, 0);   // (b, rn b, Y, sy)
@@ -786,9 +797,9 @@ __device__ __forceinline__ void core_quads(Smem &S, int warp, int lane, unsigned
             const float kk = (float)(u - quadi(q, 2).x);
             v = p5.z * core_re<float>(fmaf(kk, p0.x, -p0.y), p5.w) - q.h;
         }
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        if ((lane & 3) == 0 && sl < total && v != 0.0f) atomicAdd(&accw[u - t0], v);
+#pragma unroll
+        for (int o = 1; o < NB; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((lane & (NB - 1)) == 0 && sl < total && v != 0.0f) atomicAdd(&accw[u - t0], v);
     }
     __syncwarp();
 }
@@ -1058,21 +1069,26 @@ __global__ void __launch_bounds__(NT, 3)
                 if (V & kVPeel)
                     q.pad = __int_as_float(wide_flags(q, tg0, tg1, g.profile == kProfVoigt));
             } else {  // past the item's lines: an empty record
+                q.c = 0;
                 q.lo = 0x3fffffff;
                 q.hi = -0x3fffffff;
                 q.gA = 1;
                 q.gB = 0;
+                q.L4 = q.cl = 1;
+                q.R4 = q.ch = 0;
                 q.pad = 0.0f;
             }
+            if ((V & ~kVPlinth) == 0) batch_summary(q, lane);
             S.rec[warp][lane] = q;
             __syncwarp();
             int qn = 0;
             if ((V & ~kVPlinth) == 0) {   // short Voigt lines, with or without the plinth
                 unsigned rmask = 0u;
-                for (int j0 = 0; j0 < 32; j0 += NLB)
-                    rmask |= do_batch<V>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0) << j0;
+                for (int j0 = 0; j0 < 32; j0 += NLS)
+                    rmask |= do_batch<V, NLS>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0)
+                             << j0;
                 drain_rest(queue, qn, S, warp, lane, t0, accb - lane);
-                core_quads(S, warp, lane, rmask, t0, t1, accb - lane);
+                core_quads<NLS>(S, warp, lane, rmask, t0, t1, accb - lane);
             } else if ((V & kVPeel) && !(V & (kVDoppler | kVBinned))) {
                 for (int j0 = 0; j0 < 32; j0 += NLB)
                     do_batch_wide<V>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0);

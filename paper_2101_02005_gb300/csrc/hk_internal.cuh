@@ -39,7 +39,7 @@ constexpr int kProfVoigt = 0, kProfLorentz = 1, kProfDoppler = 2, kProfBinned = 
 //   200  <= r2 < 2500   3-node Gauss-Hermite                      7e-7
 //   64   <= r2 < 200    4-node Gauss-Hermite                      1e-6
 //   r2 < 64             trapezoid on (i/pi) int e^{-t^2}/(z-t) dt with
-//                       step 1/2, |t| <= 5.75 (FP64; 4.75 in FP32), plus the pole correction
+//                       step 1/2, |t| <= 5.75 (FP64; t in [-4, 4.75] in FP32), plus the pole correction
 //                       2 e^{-z^2}/(1 -/+ e^{-2 pi i z/h}) and a half-step
 //                       shift of the nodes when x is near one
 //                       (Chiarella & Reichel 1968; Matta & Reichel 1971)
@@ -173,16 +173,26 @@ template <typename R> __device__ __forceinline__ R core_re(R x, R y)
     bool sh = !(fr > R(0.25) && fr < R(0.75));  // x within h/4 of a node: shift lattice
     R off = sh ? R(0.5) : R(0);
     R s = R(0);
-    // float: nodes |t| <= 4.5 (shifted: -4.25 .. 4.75); the dropped terms are below
-    // 1e-8 of Re w for every r2 < 64 (|x - t| >= 1/8 by the lattice shift)
-    constexpr int NMAX = sizeof(R) == 4 ? 9 : 11;
     // nodes t = (n + off) / 2: x - t = (x - off / 2) - n / 2
     const R axs = ax - off * R(0.5);
+    if constexpr (sizeof(R) == 4) {
+        // float: nodes n = -8 .. 9, i.e. t in [-4, 4.5] (shifted: [-3.75, 4.75]);
+        // with |x| >= 0 the dropped terms are below 1e-8 of Re w for every
+        // r2 < 64 (|x - t| >= 1/8 by the lattice shift; 6e-9 against scipy's
+        // wofz in exact arithmetic)
 #pragma unroll
-    for (int n = -NMAX; n <= NMAX; ++n) {
-        R wt = sh ? R(w1[n + 11]) : R(w0[n + 11]);
-        R d = axs - R(0.5 * n);
-        s += Math<R>::div_(wt, d * d + Y);
+        for (int n = -8; n <= 9; ++n) {
+            R wt = sh ? R(w1[n + 11]) : R(w0[n + 11]);
+            R d = axs - R(0.5 * n);
+            s += Math<R>::div_(wt, d * d + Y);
+        }
+    } else {
+#pragma unroll
+        for (int n = -11; n <= 11; ++n) {
+            R wt = sh ? R(w1[n + 11]) : R(w0[n + 11]);
+            R d = axs - R(0.5 * n);
+            s += Math<R>::div_(wt, d * d + Y);
+        }
     }
     R re = R(0.5 * kInvPi) * y * s;       // (h / pi) y sum e^{-t^2} / ((x-t)^2 + y^2)
     if (y < R(2)) {
