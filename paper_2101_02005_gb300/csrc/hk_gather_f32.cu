@@ -17,8 +17,11 @@
 //   line centre.  The bands form nested intervals of group indices around
 //   the centre, computed once per line, so each group runs one formula with
 //   no divergence.  Bins of the central groups that fall in the core band
-//   (r2 < 64) go to a per-warp queue and are evaluated 32 at a time.  The
-//   Lorentzian profile is the one-node band on every group; the Doppler and
+//   (r2 < 64) are evaluated 32 at a time as (bin, line) slots: per line from
+//   a per-warp queue, per batch of co-located short lines from the batch's
+//   core and ring ranges (the trapezoid rule inside the ring radius, the
+//   8-node Gauss-Hermite rule between it and r2 = 64).  The Lorentzian
+//   profile is the one-node band on every group; the Doppler and
 //   binned-Gaussian profiles run one formula per line in their own instances.
 // * Each warp adds into its own FP32 copy of the tile in shared memory
 //   (consecutive bins, no bank conflicts, no atomics); every FLUSH_ROUNDS
@@ -59,7 +62,7 @@ struct __align__(16) Rec {
     float Ca, Cb, sa, sb;       // 2 tau Y + tau^2 for both 4-node pairs, 2 W sy      (4 nodes)
     int c, gA, gB, lo;          // nearest bin to the centre; the line's groups; first bin in the cut
     int hi, L4, R4, cl;         // last bin; groups of band gh4 or inner; first core bin
-    int ch, Lc, Rc, L2;         // last core bin (core bins: r2 < 64); groups holding core bins;
+    int ch, Lc, Rc, L2;         // last core bin (core: r2 < R8(y)); bins with r2 < 64;
     int R2;                     //   groups of band gh2 or inner
     float rn, s, y;             // centre offset from bin c, scaled strength, Gamma_L / alpha_D
     float h, k2a, k2b, pad;     // the plinth s Re w(x_cut + iy) (or 0); Y - 1/2, 2 Y (2 nodes;
@@ -106,6 +109,48 @@ __device__ __forceinline__ void band_groups(float R, float Y, float b, float rn,
         *L = lo;
         *R_ = hi;
     }
+}
+
+// Inner radius (in r2) of the ring where the 8-node Gauss-Hermite rule
+// serves the short-line batches in place of the trapezoid: 26, or more where
+// y is so small that exp(-x^2), which a Gauss-Hermite sum cannot represent,
+// would exceed ~1e-7 of Re w ~ y / (sqrt(pi) x^2) (x^2 < 64 in the bound).
+// Checked against scipy's wofz in exact arithmetic: at most 1.3e-7 relative
+// error over 26 <= r2 < 64, y from 1e-9 to 8.
+__device__ __forceinline__ float ring_r2(float y)
+{
+    return fminf(64.0f, fmaxf(26.0f, __logf(1.13e9f / y)));
+}
+
+// 8-node Gauss-Hermite value sy F8 of one pair (r2 = x^2 + y^2 at least the
+// line's ring radius): the four node pairs +-t_j (tau_j = t_j^2, normalised
+// weights 2 W_j) give F8 = sum_j 2 W_j (r2 + tau_j) / D_j,
+// D_j = r2^2 - 2 tau_j X + 2 tau_j Y + tau_j^2, summed over one common
+// denominator: one reciprocal.  D_j >= (r2 - tau_j)^2 >= 300, and for
+// r2 <= 4096 D_j <= 1.7e7, so the products stay inside the float range.  A
+// line of the batch far outside its own ring there (a huge y, or a much
+// narrower line) has r2 > 4096 and takes the two-node rule, valid and within
+// ~1.5e-7 for r2 >= 2500 (the sweeps' own rule there).
+__device__ __forceinline__ float gh8_val(float x, float Y, float sy)
+{
+    constexpr float t1 = 0.14530352150331709f, t2 = 1.3390972881263614f,
+                    t3 = 3.9269635013582872f, t4 = 8.5886356890120343f;
+    constexpr float w1 = 0.74602451535815470f, w2 = 0.23447981532351803f,
+                    w3 = 0.019270440241576534f, w4 = 0.00022522907675073554f;
+    const float X = x * x, r2 = X + Y;
+    if (r2 > 4096.0f) {
+        const float Xp = fmaf(x, x, Y - 0.5f);   // X' = x^2 + Y - 1/2
+        return fmaf(Xp, sy, sy) * rcp_ftz(fmaf(Xp, Xp, 2.0f * Y));
+    }
+    const float D1 = fmaf(r2, r2, fmaf(-2.0f * t1, X, fmaf(2.0f * t1, Y, t1 * t1)));
+    const float D2 = fmaf(r2, r2, fmaf(-2.0f * t2, X, fmaf(2.0f * t2, Y, t2 * t2)));
+    const float D3 = fmaf(r2, r2, fmaf(-2.0f * t3, X, fmaf(2.0f * t3, Y, t3 * t3)));
+    const float D4 = fmaf(r2, r2, fmaf(-2.0f * t4, X, fmaf(2.0f * t4, Y, t4 * t4)));
+    const float n1 = fmaf(w1, r2, w1 * t1), n2 = fmaf(w2, r2, w2 * t2);
+    const float n3 = fmaf(w3, r2, w3 * t3), n4 = fmaf(w4, r2, w4 * t4);
+    const float D12 = D1 * D2, D34 = D3 * D4;
+    const float num = fmaf(fmaf(n1, D2, n2 * D1), D34, fmaf(n3, D4, n4 * D3) * D12);
+    return sy * num * rcp_ftz(D12 * D34);
 }
 
 __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t l, int scale,
@@ -165,19 +210,25 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
     }
     band_groups(1.5e6f, Y, b, q.rn, c, q.gA, q.gB, &q.L2, &q.R2);
     band_groups(2500.0f, Y, b, q.rn, c, q.L2, q.R2, &q.L4, &q.R4);
-    band_groups(64.0f, Y, b, q.rn, c, q.L4, q.R4, &q.Lc, &q.Rc);
-    // the core bins themselves, c + k with |k - rn| < sqrt(64 - Y) / b, inside
-    // [lo, hi] (inside the core groups: those take a wider margin); empty: cl > ch
-    q.cl = 1;
-    q.ch = 0;
+    // bins c + k with |k - rn| < sqrt(R - Y) / b, inside [lo, hi] (inside the
+    // four-node groups: those take a wider margin); empty: first > last.
+    // R = 64: the trapezoid's band [Lc, Rc]; R = R8 (y): the inner core
+    // [cl, ch], the ring between them being the 8-node rule's (short lines).
+    q.cl = q.Lc = 1;
+    q.ch = q.Rc = 0;
     if (any && Y < 64.0f) {
-        const float Dc = fminf(sqrtf(64.0f - Y) / b, 1.0e9f);
-        const int kl = (int)floorf(q.rn - Dc) + 1, kh = (int)ceilf(q.rn + Dc) - 1;
-        const int a = max(c + kl, lo), e = min(c + kh, hi);
-        if (a <= e) {
-            q.cl = a;
-            q.ch = e;
-        }
+        auto bins = [&](float R, int *first, int *last) {
+            const float Dc = fminf(sqrtf(R - Y) / b, 1.0e9f);
+            const int kl = (int)floorf(q.rn - Dc) + 1, kh = (int)ceilf(q.rn + Dc) - 1;
+            const int a = max(c + kl, lo), e = min(c + kh, hi);
+            if (a <= e) {
+                *first = a;
+                *last = e;
+            }
+        };
+        bins(64.0f, &q.Lc, &q.Rc);
+        const float R8 = ring_r2(y);
+        if (Y < R8) bins(R8, &q.cl, &q.ch);
     }
     q.pad = 0.0f;
     if (g.profile == kProfLorentz) {          // (y/sqrt(pi)) s / r2 on every bin: all one-node
@@ -575,11 +626,13 @@ __device__ __forceinline__ int4 quadi(const Rec &q, int i)
 
 // The structure of each batch of NLS consecutive lines (lanes NLS k ..
 // NLS k + NLS - 1 of the record stage), taken lane-parallel by shuffles and
-// kept in the batch's first record, in fields the short-line path does not
-// otherwise read: Lc, Rc = the smallest L4 and the largest R4 of the lines
-// with a four-node band; L2, R2 = the union of the lines' core bin ranges
-// (empty: INT_MAX, INT_MIN); pad = flags, bit 0 when the lines share c, gA
-// and gB (gA <= gB), bit 1 when they share their cut range [lo, hi].
+// kept in the batch's first two records, in fields the short-line path does
+// not otherwise read.  First record: Lc, Rc = the smallest L4 and the largest
+// R4 of the lines with a four-node band; L2, R2 = U, the union of the lines'
+// inner core ranges [cl, ch] (empty: INT_MAX, INT_MIN); pad = flags, bit 0
+// when the lines share c, gA and gB (gA <= gB), bit 1 when they share their
+// cut range [lo, hi].  Second record: Lc, Rc = U8, the union of the lines'
+// r2 < 64 ranges (U lies inside U8).
 __device__ __forceinline__ void batch_summary(Rec &q, int lane)
 {
     constexpr unsigned FULL = 0xffffffffu, kAll = (1u << NLS) - 1u;
@@ -591,15 +644,22 @@ __device__ __forceinline__ void batch_summary(Rec &q, int lane)
     const bool same = (c0 == q.c) & (gA0 == q.gA) & (gB0 == q.gB) & (q.gA <= q.gB);
     const bool scut = (lo0 == q.lo) & (hi0 == q.hi);
     const unsigned ms = __ballot_sync(FULL, same), mc = __ballot_sync(FULL, scut);
-    const bool has4 = q.L4 <= q.R4, hasc = q.cl <= q.ch;
+    const bool has4 = q.L4 <= q.R4, hasc = q.cl <= q.ch, has8 = q.Lc <= q.Rc;
     int a = has4 ? q.L4 : INT_MAX, e = has4 ? q.R4 : INT_MIN;
     int u = hasc ? q.cl : INT_MAX, v = hasc ? q.ch : INT_MIN;
+    int u8 = has8 ? q.Lc : INT_MAX, v8 = has8 ? q.Rc : INT_MIN;
 #pragma unroll
     for (int o = 1; o < NLS; o <<= 1) {
         a = min(a, __shfl_xor_sync(FULL, a, o));
         e = max(e, __shfl_xor_sync(FULL, e, o));
         u = min(u, __shfl_xor_sync(FULL, u, o));
         v = max(v, __shfl_xor_sync(FULL, v, o));
+        u8 = min(u8, __shfl_xor_sync(FULL, u8, o));
+        v8 = max(v8, __shfl_xor_sync(FULL, v8, o));
+    }
+    if (lane == first + 1) {
+        q.Lc = u8;
+        q.Rc = v8;
     }
     if (lane == first) {
         q.Lc = a;
@@ -623,6 +683,7 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
     // the batch's structure, from the summary in its first record
     const int4 s0 = quadi(R[0], 2);   // (c, gA, gB, lo)
     const int4 s4 = quadi(R[0], 4);   // (ch, smallest L4, largest R4, first bin of U)
+    static_assert(NB >= 2, "the batch summary spans two records");
     const int c0 = s0.x, gA = s0.y, gB = s0.z, lo0 = s0.w, mL4 = s4.y, MR4 = s4.z;
     const int flags = __float_as_int(R[0].pad);
     const bool central = mL4 <= MR4;
@@ -703,15 +764,16 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
     interior(gA + 1, mL4 - 1);
     interior(MR4 + 1, gB - 1);
     // the central groups: the four-node rule (valid for every r2 >= 64) for
-    // every bin outside the batch's core bins U, summed over the batch; U is
-    // the union of the lines' core ranges (r2 < 64), and the caller's core
-    // pass evaluates every line at every bin of U with the trapezoid rule.
+    // every bin outside U8, summed over the batch; U8 is the union of the
+    // lines' r2 < 64 ranges, and the caller's core and ring passes evaluate
+    // every line at every bin of U8 (the trapezoid rule on U, the union of the
+    // inner cores; the 8-node rule on the rest).
     // The two-node parameters are dead here, which keeps the registers in
     // bounds.
     const int c0g = max(mL4, tg0), c1g = min(MR4, tg1);
     if (c0g > c1g) return kAll;
-    int ulo = s4.w, uhi = R[0].R2;   // U (empty: ulo > uhi)
-    if (ulo > uhi) {   // no core bins: a U no bin can meet
+    int ulo = R[1].Lc, uhi = R[1].Rc;   // U8 (empty: ulo > uhi)
+    if (ulo > uhi) {   // no core bins: a U8 no bin can meet
         ulo = 0x3fffffff;
         uhi = ulo;
     }
@@ -734,31 +796,48 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
     return kAll;
 }
 
-// The core bins of the batches whose lines took the batched sweep (`mask`: 4
-// bits per batch).  Each line's core bins (r2 < 64) are a contiguous range
-// (Rec::cl .. ch) and the 4 lines of a batch share their centre bin, so they
-// lie in one short union range U of bins, which the batched sweep left out
-// for all 4 lines.  Here every line takes every bin of U inside its cut with
-// the trapezoid rule (valid for any r2; a bin of U outside a line's own core
-// range is one it would otherwise have taken with the four-node rule).  The
-// pairs of all such batches are laid end to end as (batch, bin u in U, line)
-// with the line innermost -- 4 slots per bin, so the lanes of an aligned quad
-// hold one bin's 4 values, summed by two shuffles and added by one lane --
-// and evaluated 32 slots at a time.  A slot whose bin lies outside its line's
-// cut adds 0.  Quads of two batches in one step may share a bin: the update is a
-// shared-memory atomic add.  The warp's queue rows serve as scratch (the
-// queue is empty here).
-template <int NB>
-__device__ __forceinline__ void core_quads(Smem &S, int warp, int lane, unsigned mask, int t0,
+// The core and ring bins of the batches whose lines took the batched sweep
+// (`mask`: NB bits per batch), from the batch summary: U, the union of the
+// lines' inner core ranges, and U8 \ U (two intervals), U8 the union of
+// their r2 < 64 ranges; the batched sweep left all of U8 out for every line
+// of the batch.  Here every line takes every bin of its set inside its cut:
+// the trapezoid rule on U (valid for any r2: a bin of U outside a line's own
+// inner core is one it would otherwise have taken with another rule), the
+// 8-node Gauss-Hermite rule on U8 \ U (every line's r2 there is at least its
+// own ring radius R8(y)).  The pairs of all such intervals are laid end to
+// end as (interval, bin u, line) with the line innermost -- NB slots per bin,
+// so the lanes of an aligned group of NB hold one bin's values, summed by
+// shuffles and added by one lane -- and evaluated 32 slots at a time.  A slot
+// whose bin lies outside its line's cut adds 0.  Groups of two intervals in
+// one step may share a bin: the update is a shared-memory atomic add.  The
+// warp's queue rows serve as scratch (the queue is empty here).
+template <int NB, bool RING>
+__device__ __forceinline__ void core_slots(Smem &S, int warp, int lane, unsigned mask, int t0,
                                            int t1, float *accw)
 {
     constexpr int NBR = 32 / NB;                      // batches per round
+    constexpr int NI = RING ? 2 * NBR : NBR;          // intervals per round
     constexpr int LG = NB == 8 ? 3 : 2;               // log2 NB
     constexpr unsigned kAll = (1u << NB) - 1u;
     int u0 = 0, nu = 0;
-    if (lane < NBR && ((mask >> (NB * lane)) & kAll) == kAll) {
-        const Rec &q = S.rec[warp][NB * lane];     // the batch summary: U = [L2, R2]
-        const int lo = max(q.L2, t0), hi = min(q.R2, t1);
+    const int kb = RING ? lane >> 1 : lane;           // this lane's batch
+    if (lane < NI && ((mask >> (NB * kb)) & kAll) == kAll) {
+        const Rec &q0 = S.rec[warp][NB * kb];         // U = [L2, R2]
+        int lo = q0.L2, hi = q0.R2;
+        if (RING) {
+            const Rec &q1 = S.rec[warp][NB * kb + 1];   // U8 = [Lc, Rc]
+            const bool right = lane & 1;
+            if (lo > hi) {   // U empty: all of U8 in the left interval
+                lo = right ? 1 : q1.Lc;
+                hi = right ? 0 : q1.Rc;
+            } else {
+                const int l8 = right ? hi + 1 : q1.Lc, h8 = right ? q1.Rc : lo - 1;
+                lo = l8;
+                hi = h8;
+            }
+        }
+        lo = max(lo, t0);
+        hi = min(hi, t1);
         if (lo <= hi) {
             u0 = lo;
             nu = hi - lo + 1;
@@ -766,36 +845,41 @@ __device__ __forceinline__ void core_quads(Smem &S, int warp, int lane, unsigned
     }
     int inc = NB * nu;
 #pragma unroll
-    for (int o = 1; o < NBR; o <<= 1) {
+    for (int o = 1; o < NI; o <<= 1) {
         const int t = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += t;
     }
-    const int total = __shfl_sync(0xffffffffu, inc, NBR - 1);
+    const int total = __shfl_sync(0xffffffffu, inc, NI - 1);
     if (total == 0) return;   // warp-uniform
-    int *pre = reinterpret_cast<int *>(S.queue[warp]);   // first slot of batch k
-    int *ub = pre + NBR;                                 // first bin of U of batch k
-    if (lane < NBR) {
+    int *pre = reinterpret_cast<int *>(S.queue[warp]);   // first slot of interval k
+    int *ub = pre + NI;                                  // first bin of interval k
+    if (lane < NI) {
         pre[lane] = inc - NB * nu;
         ub[lane] = u0;
     }
     __syncwarp();
     for (int base = 0; base < total; base += 32) {
         const int sl = base + lane;
-        // the last batch whose first slot is <= sl (batches without core
-        // slots share their successor's first slot)
+        // the last interval whose first slot is <= sl (empty intervals share
+        // their successor's first slot)
         int k = 0;
 #pragma unroll
-        for (int st = NBR / 2; st > 0; st >>= 1)
-            if (k + st < NBR && pre[k + st] <= sl) k += st;
+        for (int st = NI / 2; st > 0; st >>= 1)
+            if (k + st < NI && pre[k + st] <= sl) k += st;
         const int rel = sl - pre[k];
         const int u = ub[k] + (rel >> LG);
-        const Rec &q = S.rec[warp][NB * k + (rel & (NB - 1))];
+        const Rec &q = S.rec[warp][NB * (RING ? k >> 1 : k) + (rel & (NB - 1))];
         float v = 0.0f;
         if (sl < total && u >= quadi(q, 2).w && u <= quadi(q, 3).x) {
             const float4 p0 = quadf(q, 0);   // (b, rn b, Y, sy)
-            const float4 p5 = quadf(q, 5);   // (R2, rn, s, y)
             const float kk = (float)(u - quadi(q, 2).x);
-            v = p5.z * core_re<float>(fmaf(kk, p0.x, -p0.y), p5.w) - q.h;
+            const float x = fmaf(kk, p0.x, -p0.y);
+            if (RING) {
+                v = gh8_val(x, p0.z, p0.w) - q.h;
+            } else {
+                const float4 p5 = quadf(q, 5);   // (R2, rn, s, y)
+                v = p5.z * core_re<float>(x, p5.w) - q.h;
+            }
         }
 #pragma unroll
         for (int o = 1; o < NB; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -1074,8 +1158,8 @@ __global__ void __launch_bounds__(NT, 3)
                 q.hi = -0x3fffffff;
                 q.gA = 1;
                 q.gB = 0;
-                q.L4 = q.cl = 1;
-                q.R4 = q.ch = 0;
+                q.L4 = q.cl = q.Lc = 1;
+                q.R4 = q.ch = q.Rc = 0;
                 q.pad = 0.0f;
             }
             if ((V & ~kVPlinth) == 0) batch_summary(q, lane);
@@ -1088,7 +1172,8 @@ __global__ void __launch_bounds__(NT, 3)
                     rmask |= do_batch<V, NLS>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0)
                              << j0;
                 drain_rest(queue, qn, S, warp, lane, t0, accb - lane);
-                core_quads<NLS>(S, warp, lane, rmask, t0, t1, accb - lane);
+                core_slots<NLS, false>(S, warp, lane, rmask, t0, t1, accb - lane);
+                core_slots<NLS, true>(S, warp, lane, rmask, t0, t1, accb - lane);
             } else if ((V & kVPeel) && !(V & (kVDoppler | kVBinned))) {
                 for (int j0 = 0; j0 < 32; j0 += NLB)
                     do_batch_wide<V>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0);
