@@ -87,8 +87,8 @@ constexpr float kWa = 2.0f * 0.4541241452319315f, kWb = 2.0f * 0.045875854768068
 
 // Groups meeting the bins c + k, |k - rn| < D with D = sqrt(R - Y) / b (widened
 // by a relative 1e-4 and 1e-3 bins so an edge group takes the more accurate
-// band), nested in [Lp, Rp]; an empty band sits at Rp + 1.
-__device__ __forceinline__ void band_groups(float R, float Y, float b, float rn, int c, int Lp,
+// band), nested in [Lp, Rp]; an empty band sits at Rp + 1.  ib = 1/b.
+__device__ __forceinline__ void band_groups(float R, float Y, float ib, float rn, int c, int Lp,
                                             int Rp, int *L, int *R_)
 {
     const float d2 = R - Y;
@@ -97,7 +97,9 @@ __device__ __forceinline__ void band_groups(float R, float Y, float b, float rn,
         *R_ = Rp;
         return;
     }
-    const float D = fminf(sqrtf(d2) / b * 1.0001f + 1e-3f, 1.0e9f);
+    // sqrt(d2) / b from the hardware reciprocal square root and reciprocal
+    // (a few ulp; the widening covers them)
+    const float D = fminf(d2 * rsqrtf(d2) * ib * 1.0001f + 1e-3f, 1.0e9f);
     const int kL = (int)floorf(rn - D) + 1, kR = (int)ceilf(rn + D) - 1;
     int lo = (c + kL) >> 5, hi = (c + kR) >> 5;   // arithmetic shifts: floor division
     lo = max(lo, Lp);
@@ -119,7 +121,7 @@ __device__ __forceinline__ void band_groups(float R, float Y, float b, float rn,
 // error over 26 <= r2 < 64, y from 1e-9 to 8.
 __device__ __forceinline__ float ring_r2(float y)
 {
-    return fminf(64.0f, fmaxf(26.0f, __logf(1.13e9f / y)));
+    return fminf(64.0f, fmaxf(26.0f, 20.845483f - __logf(y)));   // ln(1.13e9) - ln y
 }
 
 // 8-node Gauss-Hermite value sy F8 of one pair (r2 = x^2 + y^2 at least the
@@ -208,8 +210,9 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
         q.gA = 1;
         q.gB = 0;
     }
-    band_groups(1.5e6f, Y, b, q.rn, c, q.gA, q.gB, &q.L2, &q.R2);
-    band_groups(2500.0f, Y, b, q.rn, c, q.L2, q.R2, &q.L4, &q.R4);
+    const float ib = rcp_ftz(b);
+    band_groups(1.5e6f, Y, ib, q.rn, c, q.gA, q.gB, &q.L2, &q.R2);
+    band_groups(2500.0f, Y, ib, q.rn, c, q.L2, q.R2, &q.L4, &q.R4);
     // bins c + k with |k - rn| < sqrt(R - Y) / b, inside [lo, hi] (inside the
     // four-node groups: those take a wider margin); empty: first > last.
     // R = 64: the trapezoid's band [Lc, Rc]; R = R8 (y): the inner core
@@ -218,7 +221,10 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
     q.ch = q.Rc = 0;
     if (any && Y < 64.0f) {
         auto bins = [&](float R, int *first, int *last) {
-            const float Dc = fminf(sqrtf(R - Y) / b, 1.0e9f);
+            // (the band edge to a few ulp: the rules on either side of it are
+            // both valid there)
+            const float d2 = R - Y;
+            const float Dc = fminf(d2 * rsqrtf(d2) * ib, 1.0e9f);
             const int kl = (int)floorf(q.rn - Dc) + 1, kh = (int)ceilf(q.rn + Dc) - 1;
             const int a = max(c + kl, lo), e = min(c + kh, hi);
             if (a <= e) {
@@ -780,6 +786,9 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
     const unsigned uspan = (unsigned)(uhi - ulo);
     // (the four-node constants are read from shared memory in the loop: a
     // 128-bit load per line and group costs less than holding them)
+    float Yc[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) Yc[j] = R[j].Y;
     float kf = (float)(32 * c0g + kfc);
     float *p = base + 32 * (c0g - tg0);
     int bin = 32 * c0g + lane;
@@ -789,7 +798,7 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
         for (int j = 0; j < NB; ++j) {
             const float4 f = quadf(R[j], 1);   // (Ca, Cb, sa, sb)
             float r2;
-            v += gh4_val(kf, b[j], nrb[j], quadf(R[j], 0).z, f.x, f.y, f.z, f.w, &r2);
+            v += gh4_val(kf, b[j], nrb[j], Yc[j], f.x, f.y, f.z, f.w, &r2);
         }
         if ((unsigned)(bin - ulo) > uspan) p[0] += v;
     }
