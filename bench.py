@@ -37,7 +37,12 @@ METRIC = "lines/s and Voigt evals/s on 1 GB300 (FP32-comp vs FP64 GPU) at stated
 # are four-node work here.  For short lines the kernel evaluates the one-node
 # region with the two-node rule (fewer passes per line); the model still counts
 # the one-node rule's 8 flops there, so it under-reports rather than inflates.
-FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 25, "gh4": 25, "core": 200}
+# ring8: the FP32C short-line batches take the part R8(y) <= r2 < 64 of the
+# core with the 8-node Gauss-Hermite rule (four D_j at 4 flops, four numerators
+# at 2, their combination over one denominator 11, the reciprocal and scaling
+# 3: 6 + 39); hk_count_ring_pairs counts those pairs, which the FP32C rooflines
+# take out of the core count.
+FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 25, "gh4": 25, "ring8": 45, "core": 200}
 # DRAM bytes per line of one k_gather_f32 launch, from the ncu capture in
 # profiles/k_gather_f32_config1-1e7-lines.md (241.4 MB read + 3.8 MB written for
 # 1e7 lines; the line list is read once, so traffic grows with the line
@@ -370,12 +375,13 @@ def batched_measure(w, hk, synth, dev, steps, warmup, peaks):
     opts = hk.make_opts(float(Q(296.0)), w.cut, hk.HK_FP32C, flags=hk.HK_SIGMA_F64)
     pts = w.states()
     states = [hk.make_state(t, p, float(Q(t))) for t, p in pts]
-    counts = [0] * 6
+    counts = [0] * 7
     for s in species:
         for st in states:
-            c = hk.hk_count_pairs(s, grid, st, opts)
+            c = hk.hk_count_pairs(s, grid, st, opts) + [hk.hk_count_ring_pairs(s, grid, st, opts)]
             counts = [a + b for a, b in zip(counts, c)]
-    bands = dict(zip(["gh1", "gh2", "gh3", "gh4", "core"], counts[1:]))
+    bands = dict(zip(["gh1", "gh2", "gh3", "gh4", "core", "ring8"], counts[1:]))
+    bands["core"] -= bands["ring8"]
     flops_step = sum(FLOPS_PER_PAIR[b] * n for b, n in bands.items())
     big = max(range(len(species)), key=lambda i: species[i].n)
     hk.hk_autotune(species[big], grid, states[len(states) // 2], opts)
@@ -648,6 +654,8 @@ def main():
     counts = hk.hk_count_pairs(D, grid, state, opts)
     pairs = counts[0]
     bands = dict(zip(["gh1", "gh2", "gh3", "gh4", "core"], counts[1:]))
+    bands["ring8"] = hk.hk_count_ring_pairs(D, grid, state, opts)
+    bands["core"] -= bands["ring8"]
     flops_step = sum(FLOPS_PER_PAIR[b] * n for b, n in bands.items())
     stream = torch.cuda.current_stream()
 

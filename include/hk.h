@@ -352,6 +352,18 @@ int hk_set_tuning(int precision, int lmax, int tile_bins);
 int hk_count_pairs(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
                    const hk_opts *opts, int64_t *counts, void *stream);
 
+/* Instrumentation (no counterpart in the paper).  Of the pairs counted in
+ * counts[5] by hk_count_pairs (r2 < 64), those that the FP32C short-line
+ * batches evaluate with the 8-node Gauss-Hermite ring rule instead of the
+ * trapezoid: R8(y) <= r2 < 64, R8(y) = max(26, ln(1.13e9 / y)) capped at 64
+ * (decided in FP64).  Nonzero only for problems that take the short-line
+ * path (HK_FP32C, the Voigt profile, a fixed cut of fewer than 1024 bins);
+ * lines of a batch that does not share its structure take the trapezoid
+ * there, so this is an upper bound.  *ring: HOST int64.  Synchronises
+ * `stream`. */
+int hk_count_ring_pairs(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
+                        const hk_opts *opts, int64_t *ring, void *stream);
+
 /* Instrumentation (no counterpart in the paper).  mode 1: start recording
  * CUDA events around every launch of the Voigt-sum kernel on the stream it
  * runs on (previous records are dropped).  mode 0: stop, wait for the

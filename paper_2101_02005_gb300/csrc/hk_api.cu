@@ -495,6 +495,33 @@ int hk_count_pairs(const hk_lines *lines, const hk_grid *grid, const hk_state *s
     return HK_OK;
 }
 
+int hk_count_ring_pairs(const hk_lines *lines, const hk_grid *grid, const hk_state *state,
+                        const hk_opts *opts, int64_t *ring, void *stream)
+{
+    int rc;
+    if ((rc = check_lines(lines, true)) || (rc = check_grid(grid)) || (rc = check_state(state)) ||
+        (rc = check_opts(opts)))
+        return rc;
+    if (!ring) return HK_EINVAL;
+    *ring = 0;
+    const GridD g = make_grid(grid, opts);
+    // the FP32C short-line batches: a fixed cut of fewer than 1024 bins, Voigt
+    const bool short_lines = opts->precision == HK_FP32C && g.profile == kProfVoigt &&
+                             g.W > 0.0 && 2.0 * g.W + 1.0 < 1024.0;
+    if (lines->n == 0 || !short_lines) return HK_OK;
+    char *ws;
+    if ((rc = pool_get(256, &ws))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Prob p = make_prob(lines, state, opts);
+    if ((rc = count_pairs_run(p, g, (unsigned long long *)ws, st, num_sms()))) return rc;
+    unsigned long long h[7];
+    cudaError_t e = cudaMemcpyAsync(h, ws, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (e) return fail_cuda(e);
+    *ring = (int64_t)h[6];
+    return HK_OK;
+}
+
 int hk_profile(int mode, double *ms, int64_t *launches)
 {
     if (mode != 0 && mode != 1) return HK_EINVAL;

@@ -450,7 +450,7 @@ __global__ void k_finalize(const Prob *__restrict__ probs, int nprob, int64_t nb
 // ---- pair / band counts (instrumentation) --------------------------------------
 __global__ void k_count_pairs(Prob p, GridD g, unsigned long long *counts)
 {
-    unsigned long long c[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long c[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < p.n;
          l += (int64_t)gridDim.x * blockDim.x) {
         // the FP32 kernels' geometry (its pair total must equal the oracle's)
@@ -480,8 +480,19 @@ __global__ void k_count_pairs(Prob p, GridD g, unsigned long long *counts)
         c[3] += inside[1] - inside[2];
         c[4] += inside[2] - inside[3];
         c[5] += inside[3];
+        // pairs with R8 <= r2 < 64, R8 = max(26, ln(1.13e9) - ln y) (at most 64):
+        // the ring the FP32C short-line batches take with the 8-node rule
+        const double R8 = fmin(64.0, fmax(26.0, 20.845483 - log(y)));
+        const double D2 = R8 - y * y;
+        unsigned long long in8 = 0;
+        if (D2 > 0.0) {
+            const double D = sqrt(D2) / b;
+            const double a = fmax(klo, floor(r - D) + 1.0), e = fmin(khi, ceil(r + D) - 1.0);
+            in8 = e >= a ? (unsigned long long)(e - a + 1.0) : 0ull;
+        }
+        c[6] += inside[3] > in8 ? inside[3] - in8 : 0ull;
     }
-    for (int t = 0; t < 6; ++t) {
+    for (int t = 0; t < 7; ++t) {
         unsigned long long v = c[t];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0 && v) atomicAdd(counts + t, v);
@@ -491,7 +502,7 @@ __global__ void k_count_pairs(Prob p, GridD g, unsigned long long *counts)
 int count_pairs_run(const Prob &p, const GridD &g, unsigned long long *counts_d, cudaStream_t st,
                     int num_sms)
 {
-    cudaError_t e = cudaMemsetAsync(counts_d, 0, 6 * sizeof(unsigned long long), st);
+    cudaError_t e = cudaMemsetAsync(counts_d, 0, 7 * sizeof(unsigned long long), st);
     if (e) return fail_cuda(e);
     k_count_pairs<<<num_sms * 4, 256, 0, st>>>(p, g, counts_d);
     if ((e = cudaGetLastError())) return fail_cuda(e);

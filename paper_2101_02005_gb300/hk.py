@@ -28,7 +28,7 @@ HK_PROFILE_VOIGT, HK_PROFILE_LORENTZ, HK_PROFILE_DOPPLER, HK_PROFILE_BINNED_GAUS
 EXPORTS = ["hk_line_strength", "hk_widths", "hk_voigt_accumulate", "hk_cross_section",
            "hk_cross_section_batched", "hk_cross_section_backward", "hk_workspace_size",
            "hk_autotune", "hk_sync_status", "hk_release", "hk_strerror", "hk_last_cuda_error",
-           "hk_constants", "hk_version", "hk_count_pairs", "hk_profile",
+           "hk_constants", "hk_version", "hk_count_pairs", "hk_count_ring_pairs", "hk_profile",
            "hk_cross_section_noalloc", "hk_tuning", "hk_cross_section_host", "hk_set_tuning",
            "hk_noalloc_status", "hk_measure_peak"]
 
@@ -97,6 +97,8 @@ def lib():
     L.hk_last_cuda_error.argtypes = []
     L.hk_constants.argtypes = [P(ctypes.c_double)]
     L.hk_version.argtypes = []
+    L.hk_count_ring_pairs.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts),
+                                      P(ctypes.c_int64), vp]
     L.hk_count_pairs.argtypes = [P(hk_lines), P(hk_grid), P(hk_state), P(hk_opts),
                                  P(ctypes.c_int64), vp]
     L.hk_profile.argtypes = [ctypes.c_int, P(ctypes.c_double), P(ctypes.c_int64)]
@@ -378,6 +380,19 @@ def hk_count_pairs(lines: DeviceLines, grid: hk_grid, state: hk_state, opts: hk_
                                                   ctypes.byref(state), ctypes.byref(opts), out,
                                                   _stream(stream)))
     return [int(v) for v in out]
+
+
+def hk_count_ring_pairs(lines: DeviceLines, grid: hk_grid, state: hk_state, opts: hk_opts,
+                        stream=None) -> int:
+    """Pairs of the core band that the FP32C short-line batches take with the
+    8-node ring rule (instrumentation; 0 for other problems)."""
+    out = ctypes.c_int64(0)
+    L = lines.struct()
+    _check("hk_count_ring_pairs", lib().hk_count_ring_pairs(ctypes.byref(L), ctypes.byref(grid),
+                                                            ctypes.byref(state),
+                                                            ctypes.byref(opts),
+                                                            ctypes.byref(out), _stream(stream)))
+    return int(out.value)
 
 
 def hk_profile(mode: int):

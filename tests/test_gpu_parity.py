@@ -747,3 +747,37 @@ def test_dense_wide_lines(hk):
                     record(what, assert_sigma_close(got, ref, what))
                 else:
                     record(what, assert_plinth_close(got, ref, base[prof], what))
+
+
+def test_ring_pair_count(hk):
+    """hk_count_ring_pairs (instrumentation for the cost model): on the
+    config-0 list (short lines, cut 25 at 0.1 cm^-1) the pairs with
+    R8(y) <= r2 < 64, R8 = max(26, ln(1.13e9 / y)) at most 64, against a count
+    from the oracle's widths and the exact cut range (a few edge pairs may fall
+    either side in float geometry); a subset of the core count; 0 for the FP64
+    form and for wide lines."""
+    w = synth.config(0)
+    L = w.species[0]
+    T, P = w.states()[0]
+    D = hk.DeviceLines.from_host(L)
+    g = hk.make_grid(*w.grid.astuple())
+    st = hk.make_state(T, P, float(Q(T)))
+    ring = hk.hk_count_ring_pairs(D, g, st, hk.make_opts(QREF, w.cut))
+    core = hk.hk_count_pairs(D, g, st, hk.make_opts(QREF, w.cut))[5]
+    aD, GL = oracle.widths(L.nu0, L.gamma_ref, L.n_T, T, P, L.mass_amu)
+    nu_min, dnu, nbins = w.grid.astuple()
+    want = 0
+    for l in range(L.n):
+        if not (L.nu0[l] > 0.0):
+            continue
+        y = GL[l] / aD[l]
+        R8 = min(64.0, max(26.0, math.log(1.13e9) - math.log(y)))
+        i = np.arange(max(0, int((L.nu0[l] - w.cut - nu_min) / dnu) - 2),
+                      min(nbins, int((L.nu0[l] + w.cut - nu_min) / dnu) + 3))
+        d = nu_min + i * dnu - L.nu0[l]
+        r2 = (d / aD[l]) ** 2 + y * y
+        want += int(np.count_nonzero((np.abs(d) <= w.cut) & (r2 >= R8) & (r2 < 64.0)))
+    assert 0 < ring < core
+    assert abs(ring - want) <= 1e-3 * want + 20, (ring, want)
+    assert hk.hk_count_ring_pairs(D, g, st, hk.make_opts(QREF, w.cut, hk.HK_FP64)) == 0
+    assert hk.hk_count_ring_pairs(D, g, st, hk.make_opts(QREF, 600.0)) == 0   # 12001 bins
