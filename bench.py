@@ -44,10 +44,10 @@ METRIC = "lines/s and Voigt evals/s on 1 GB300 (FP32-comp vs FP64 GPU) at stated
 # take out of the core count.
 FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 25, "gh4": 25, "ring8": 45, "core": 200}
 # DRAM bytes per line of one k_gather_f32 launch, from the ncu capture in
-# profiles/k_gather_f32_config1-1e7-lines.md (241.4 MB read + 3.8 MB written for
+# profiles/k_gather_f32_config1-1e7-lines.md (242.2 MB read + 3.5 MB written for
 # 1e7 lines; the line list is read once, so traffic grows with the line
 # count).  Set to None when the kernel changes.
-GATHER_DRAM_BYTES_PER_LINE = 24.52
+GATHER_DRAM_BYTES_PER_LINE = 24.57
 FP32_LANES_PER_SM = 128
 
 
@@ -711,7 +711,7 @@ def main():
         "traffic": traffic,
         "traffic_basis": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 1e7-line "
                           "launch of this kernel (profiles/k_gather_f32_config1-1e7-lines.md), "
-                          "24.5 B per line, scaled by the line count" if traffic else None),
+                          "24.6 B per line, scaled by the line count" if traffic else None),
         "algorithmic_bytes": 24 * L.n, "gather_ms_per_launch": g_ms,
         "gather_share_of_step": g_ms / ms_step if ms_step else None,
         "flops_per_step": flops_step, "cost_model": FLOPS_PER_PAIR,
