@@ -886,6 +886,15 @@ int hk_noalloc_status(void *stream)
     return HK_OK;
 }
 
+// Whether the problems of one species in a batched call share each line's
+// bin geometry (a fixed cut or none, no pressure shift), and there are enough
+// of them for a geometry prepass to pay.
+static bool shared_geometry(const hk_lines &L, int nTP, const hk_opts *opts)
+{
+    return nTP >= 2 && L.n > 0 && !L.delta && opts->cut_mode != HK_CUT_DOPPLER &&
+           opts->cut_mode != HK_CUT_LORENTZ;
+}
+
 int hk_workspace_size(int kind, const hk_lines *species, int nspecies, int nTP,
                       const hk_grid *grid, const hk_opts *opts, size_t *bytes)
 {
@@ -902,6 +911,8 @@ int hk_workspace_size(int kind, const hk_lines *species, int nspecies, int nTP,
                 size_t cb;
                 total += al(sort_bytes(species[s].n, &cb));
             }
+            if (shared_geometry(species[s], nTP, opts))
+                total += al((size_t)species[s].n * sizeof(int4));
         }
     } else {
         if ((rc = check_lines(&species[0], true))) return rc;
@@ -943,11 +954,23 @@ int hk_cross_section_batched(const hk_lines *species, int nspecies, const hk_sta
             sort_ws += al(sort_bytes(species[s].n, &cb));
         }
     }
+    GridD g = make_grid(grid, opts);
     std::vector<Prob> probs;
     probs.reserve((size_t)nspecies * nTP);
-    for (int s = 0; s < nspecies; ++s)
-        for (int k = 0; k < nTP; ++k) probs.push_back(make_prob(&L[s], &TP[k], opts));
-    GridD g = make_grid(grid, opts);
+    for (int s = 0; s < nspecies; ++s) {
+        // each line's bin geometry once for all (T, P) points when they share it
+        int4 *geo = nullptr;
+        if (shared_geometry(species[s], nTP, opts)) {
+            geo = (int4 *)sort_ws;
+            sort_ws += al((size_t)species[s].n * sizeof(int4));
+            if ((rc = line_geo_launch(make_prob(&L[s], &TP[0], opts), g, geo, st, num_sms())))
+                return rc;
+        }
+        for (int k = 0; k < nTP; ++k) {
+            probs.push_back(make_prob(&L[s], &TP[k], opts));
+            probs.back().geo = geo;
+        }
+    }
     unsigned *sw = status_word();
     if (!sw) return HK_ENOMEM;
     return gather_run(probs.data(), (int)probs.size(), g, HK_FP32C, t.bpt, t.lmax, sigma_out,

@@ -162,7 +162,21 @@ __device__ __forceinline__ void make_rec(const Prob &pr, const GridD &g, int64_t
     int c, lo, hi;
     float rn;
     CutW cw;
-    const bool any = line_geometry_cut(pr, g, l, &cw, &c, &rn, &lo, &hi);
+    bool any;
+    if (pr.geo) {   // computed once for all problems of the line list (fixed cut or none)
+        const int4 G = pr.geo[l];
+        c = G.x;
+        rn = __int_as_float(G.y);
+        lo = G.z;
+        hi = G.w;
+        any = lo <= hi;
+        cw.nocut = !(g.W > 0.0);
+        cw.W = g.W;
+        cw.Wi = g.Wi;
+        cw.Wf = g.Wf;
+    } else {
+        any = line_geometry_cut(pr, g, l, &cw, &c, &rn, &lo, &hi);
+    }
     q.c = c;
     q.lo = lo;
     q.hi = hi;
@@ -1214,6 +1228,30 @@ __global__ void __launch_bounds__(NT, 3)
 }
 
 }  // namespace f32g
+
+// Each line's bin geometry as the FP32C records take it (c, rn, lo, hi; an
+// empty range when no bin of the grid is inside the cut), for a line list
+// whose problems share it: a fixed cut or none and no pressure shift, so that
+// the geometry depends on the line and the grid only.
+__global__ void k_line_geo(Prob p, GridD g, int4 *geo)
+{
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < p.n;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        int c, lo, hi;
+        float rn;
+        CutW cw;
+        line_geometry_cut(p, g, l, &cw, &c, &rn, &lo, &hi);
+        geo[l] = make_int4(c, __float_as_int(rn), lo, hi);
+    }
+}
+
+int line_geo_launch(const Prob &p, const GridD &g, int4 *geo, cudaStream_t st, int num_sms)
+{
+    if (p.n <= 0) return HK_OK;
+    k_line_geo<<<num_sms * 4, 256, 0, st>>>(p, g, geo);
+    const cudaError_t e = cudaGetLastError();
+    return e ? fail_cuda(e) : HK_OK;
+}
 
 // Dynamic shared memory of a launch with `tile`-bin tiles.
 static size_t f32_smem(int tile) { return sizeof(f32g::Smem) + (size_t)(f32g::NW + 2) * tile * 4; }

@@ -308,6 +308,10 @@ struct Prob {
     float press_air_f, press_self_f;
     double K_D;                 // sqrt(ln 2) sqrt(2 k_B T / m) / c: Gamma_D = nu0 K_D
     const double *cutmax;       // device: largest cutting length of the lines (per-line modes)
+    // device: each line's bin geometry (c, rn as float bits, lo, hi), computed
+    // once for problems that share it (a fixed cut or none, no pressure shift),
+    // or null (the FP32C kernel then computes it per record)
+    const int4 *geo;
     // the same scalars rounded to float (set with them on the host), for the
     // FP32 strength; K2 as a float pair K2_hi + K2_lo (about 48 bits)
     float qratio_f, c2T_f, c2Tref_f, mass_scale_f, aD_coef_f, log2_tratio_f, press_f,

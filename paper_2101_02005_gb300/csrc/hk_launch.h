@@ -48,6 +48,8 @@ int gather_f32_launch(const Prob *probs_d, const GridD &g, int64_t ntiles, int64
 // Profiling of the gather launches (hk_profile).
 void gather_profile_record(cudaStream_t st, bool begin);
 int gather_profile(int mode, double *ms, int64_t *launches);
+// Per-line bin geometry shared by the problems of a line list (hk_gather_f32.cu).
+int line_geo_launch(const Prob &p, const GridD &g, int4 *geo, cudaStream_t st, int num_sms);
 // Pair and band counts (hk_count_pairs).
 int count_pairs_run(const Prob &p, const GridD &g, unsigned long long *counts_d, cudaStream_t st,
                     int num_sms);
