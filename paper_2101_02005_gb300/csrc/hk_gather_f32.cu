@@ -691,12 +691,130 @@ __device__ __forceinline__ void batch_summary(Rec &q, int lane)
     }
 }
 
+// ---- a round's two-node interiors as one series in 1/x ---------------------
+//
+// When the 32 lines of a warp's round share their nearest bin c and their
+// groups gA, gB (dense sorted lists), the groups where every line is inside its
+// cut and in the two-node band -- [gA + 1, min L4 - 1] and [max R4 + 1, gB - 1]
+// over the round -- take all 32 lines at once.  A line's two-node value is two
+// Lorentzians, sy / 2 [1 / ((x_j - t)^2 + Y) + 1 / ((x_j + t)^2 + Y)],
+// t = 1/sqrt(2).  With x = (k - rn_0) b_0 the offset of bin c + k from line 0
+// and x_j = beta_j x + d_j (beta_j = b_j / b_0, d_j = (rn_0 - rn_j) b_j), each
+// Lorentzian is 1 / (beta_j^2 ((x - a)^2 + c^2)) = Im(1 / (x - z)) / (beta_j^2 c),
+// z = a + i c, a = (+-t - d_j) / beta_j, c = y_j / beta_j, and
+// 1 / (x - z) = sum_k z^k / x^(k+1) for |x| > |z|.  So the round's sum is
+// sum_k B_k / x^(k+1), B_k = sum over lines and nodes of
+// s_j / (2 sqrt(pi) beta_j) Im(z^k) (Im z^0 = 0): seven coefficients, taken
+// lane-parallel (lane j, line j) and summed over the warp, then per bin one
+// reciprocal and a Horner sum for the whole round instead of 6 instructions per
+// line.  The series is used when every |z| <= 3: in the two-node band
+// r2 >= 2500, so |x| >= ~47 there, and the terms after z^7 stay below
+// 8 (3/47)^7 = 3.5e-8 of the sum (5e-9 against the direct two-node sums in
+// FP64 over seeded rounds with y up to 2.2 and offsets across a whole bin).
+constexpr int KMP = 7;   // series terms
+constexpr float kTnode = 0.70710678118654752f;
+
+struct RoundSeries {
+    float B[KMP + 1];   // B[1..KMP]
+    float b0, nrb0, H;
+    int c0, RA, RB;     // the series covers groups [gA + 1, RA - 1] and [RB + 1, gB - 1]
+                        //   (disjoint: RA <= RB + 1)
+    bool on;
+};
+
+// Decides whether the round takes the series and, if so, its coefficients.
+// q: this lane's record (line `lane` of the round).  Called by the whole warp.
+template <int V>
+__device__ __forceinline__ void round_series(const Rec &q, int lane, RoundSeries &rs)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    rs.on = false;
+    const int c0 = __shfl_sync(FULL, q.c, 0), gA = __shfl_sync(FULL, q.gA, 0),
+              gB = __shfl_sync(FULL, q.gB, 0);
+    const float b0 = __shfl_sync(FULL, q.b, 0), rn0 = __shfl_sync(FULL, q.rn, 0);
+    const bool has4 = q.L4 <= q.R4;
+    int mL4 = has4 ? q.L4 : INT_MAX, MR4 = has4 ? q.R4 : INT_MIN;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mL4 = min(mL4, __shfl_xor_sync(FULL, mL4, o));
+        MR4 = max(MR4, __shfl_xor_sync(FULL, MR4, o));
+    }
+    // this line's two nodes
+    const float beta = q.b / b0;
+    const float ib = 1.0f / beta;
+    const float d = (rn0 - q.rn) * q.b;
+    const float ap = (kTnode - d) * ib, am = (-kTnode - d) * ib, cc = q.y * ib;
+    const float c2 = cc * cc;
+    const bool ok = (c0 == q.c) & (gA == q.gA) & (gB == q.gB) & (gA <= gB) &
+                    (fmaf(ap, ap, c2) <= 9.0f) & (fmaf(am, am, c2) <= 9.0f) &
+                    (mL4 > MR4 || (mL4 > gA && MR4 < gB));
+    if (!__all_sync(FULL, ok)) return;   // warp-uniform
+    const float wt = q.s * (float)(0.5 * kInvSqrtPi) * ib;
+    float B[KMP + 1];
+    B[0] = 0.0f;
+#pragma unroll
+    for (int k = 1; k <= KMP; ++k) B[k] = 0.0f;
+#pragma unroll
+    for (int sgn = 0; sgn < 2; ++sgn) {
+        const float a = sgn ? am : ap;
+        float zr = a, zi = cc;
+#pragma unroll
+        for (int k = 1; k <= KMP; ++k) {
+            B[k] = fmaf(wt, zi, B[k]);
+            const float nr = fmaf(zr, a, -zi * cc), ni = fmaf(zr, cc, zi * a);
+            zr = nr;
+            zi = ni;
+        }
+    }
+    float H = (V & kVPlinth) ? q.h : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 1; k <= KMP; ++k) B[k] += __shfl_xor_sync(FULL, B[k], o);
+        if (V & kVPlinth) H += __shfl_xor_sync(FULL, H, o);
+    }
+#pragma unroll
+    for (int k = 0; k <= KMP; ++k) rs.B[k] = B[k];
+    rs.b0 = b0;
+    rs.nrb0 = -rn0 * b0;
+    rs.H = H;
+    rs.c0 = c0;
+    if (mL4 <= MR4) {
+        rs.RA = mL4;
+        rs.RB = MR4;
+    } else {   // no four-node band in the round: all of [gA + 1, gB - 1] on the left
+        rs.RA = gB;
+        rs.RB = gB - 1;
+    }
+    rs.on = true;
+}
+
+// The series over groups [g0, g1] of the tile (p: the warp's tile copy at g0).
+__device__ __forceinline__ void round_sweep(const RoundSeries &rs, int g0, int g1, int tg0,
+                                            int tg1, float *base, int lane)
+{
+    g0 = max(g0, tg0);
+    g1 = min(g1, tg1);
+    if (g0 > g1) return;
+    float kf = (float)(32 * g0 + lane - rs.c0);
+    float *p = base + 32 * (g0 - tg0);
+    float *const pe = base + 32 * (g1 - tg0);
+    for (; p <= pe; p += 32, kf += 32.0f) {
+        const float x = fmaf(kf, rs.b0, rs.nrb0);
+        const float w = rcp_ftz(x);
+        float h = rs.B[KMP];
+#pragma unroll
+        for (int k = KMP - 1; k >= 1; --k) h = fmaf(h, w, rs.B[k]);
+        p[0] += fmaf(h, w * w, -rs.H);
+    }
+}
+
 // Returns the lines (bit j for line j0 + j) whose core bins are left to the
 // caller's core-range pass: those of a batch that took the batched sweep.
 template <int V, int NB>
 __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0, int tg1,
                                              float *base, int lane, unsigned *queue, int &qn,
-                                             int t0)
+                                             int t0, int RA, int RB)
 {
     constexpr unsigned kAll = (1u << NB) - 1u;
     const Rec *R = &S.rec[warp][j0];
@@ -777,12 +895,14 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
     edge(gA);
     if (gB == gA) return kAll;
     edge(gB);
+    // (the round's series covers [gA + 1, RA - 1] and [RB + 1, gB - 1]; with no
+    // series RA = gA + 1 and RB = gB - 1, which cover nothing)
     if (!central) {
-        interior(gA + 1, gB - 1);
+        interior(max(gA + 1, RA), min(gB - 1, RB));
         return kAll;
     }
-    interior(gA + 1, mL4 - 1);
-    interior(MR4 + 1, gB - 1);
+    interior(max(gA + 1, RA), mL4 - 1);
+    interior(MR4 + 1, min(gB - 1, RB));
     // the central groups: the four-node rule (valid for every r2 >= 64) for
     // every bin outside U8, summed over the batch; U8 is the union of the
     // lines' r2 < 64 ranges, and the caller's core and ring passes evaluate
@@ -1190,9 +1310,21 @@ __global__ void __launch_bounds__(NT, 3)
             __syncwarp();
             int qn = 0;
             if ((V & ~kVPlinth) == 0) {   // short Voigt lines, with or without the plinth
+                // the round's two-node interiors as one series, when it can take it
+                RoundSeries rs;
+                round_series<V>(q, lane, rs);
+                int RA = INT_MIN, RB = INT_MAX;
+                if (rs.on) {   // warp-uniform
+                    const int gA = S.rec[warp][0].gA, gB = S.rec[warp][0].gB;
+                    round_sweep(rs, gA + 1, rs.RA - 1, tg0, tg1, accb, lane);
+                    round_sweep(rs, rs.RB + 1, gB - 1, tg0, tg1, accb, lane);
+                    RA = rs.RA;
+                    RB = rs.RB;
+                }
                 unsigned rmask = 0u;
                 for (int j0 = 0; j0 < 32; j0 += NLS)
-                    rmask |= do_batch<V, NLS>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0)
+                    rmask |= do_batch<V, NLS>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0,
+                                              RA, RB)
                              << j0;
                 drain_rest(queue, qn, S, warp, lane, t0, accb - lane);
                 core_slots<NLS, false>(S, warp, lane, rmask, t0, t1, accb - lane);
