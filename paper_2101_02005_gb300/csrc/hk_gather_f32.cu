@@ -691,44 +691,53 @@ __device__ __forceinline__ void batch_summary(Rec &q, int lane)
     }
 }
 
-// ---- a round's two-node interiors as one series in 1/x ---------------------
+// ---- a round's lines as one series in 1/x ------------------------------------
 //
 // When the 32 lines of a warp's round share their nearest bin c and their
-// groups gA, gB (dense sorted lists), the groups where every line is inside its
-// cut and in the two-node band -- [gA + 1, min L4 - 1] and [max R4 + 1, gB - 1]
-// over the round -- take all 32 lines at once.  A line's two-node value is two
-// Lorentzians, sy / 2 [1 / ((x_j - t)^2 + Y) + 1 / ((x_j + t)^2 + Y)],
-// t = 1/sqrt(2).  With x = (k - rn_0) b_0 the offset of bin c + k from line 0
-// and x_j = beta_j x + d_j (beta_j = b_j / b_0, d_j = (rn_0 - rn_j) b_j), each
-// Lorentzian is 1 / (beta_j^2 ((x - a)^2 + c^2)) = Im(1 / (x - z)) / (beta_j^2 c),
-// z = a + i c, a = (+-t - d_j) / beta_j, c = y_j / beta_j, and
-// 1 / (x - z) = sum_k z^k / x^(k+1) for |x| > |z|.  So the round's sum is
-// sum_k B_k / x^(k+1), B_k = sum over lines and nodes of
-// s_j / (2 sqrt(pi) beta_j) Im(z^k) (Im z^0 = 0): seven coefficients, taken
-// lane-parallel (lane j, line j) and summed over the warp, then per bin one
-// reciprocal and a Horner sum for the whole round instead of 6 instructions per
-// line.  The series is used when every |z| <= 3: in the two-node band
-// r2 >= 2500, so |x| >= ~47 there, and the terms after z^7 stay below
-// 8 (3/47)^7 = 3.5e-8 of the sum (5e-9 against the direct two-node sums in
-// FP64 over seeded rounds with y up to 2.2 and offsets across a whole bin).
-constexpr int KMP = 7;   // series terms
+// groups gA, gB (dense sorted lists), their sum over the groups between the
+// edge groups can be taken for all 32 lines at once.  A Gauss-Hermite value of
+// a line is a sum of Lorentzians: (y/sqrt(pi)) sum_k W_k / ((x_j - t_k)^2 + y^2)
+// over its nodes t_k.  With x = (k - rn_0) b_0 the offset of bin c + k from
+// line 0 and x_j = beta_j x + d_j (beta_j = b_j / b_0, d_j = (rn_0 - rn_j) b_j),
+// each Lorentzian is 1 / (beta_j^2 ((x - a)^2 + c^2)) = Im(1 / (x - z)) / (beta_j^2 c),
+// z = a + i c, a = (t_k - d_j) / beta_j, c = y_j / beta_j, and
+// 1 / (x - z) = sum_m z^m / x^(m+1) for |x| > |z|.  So the round's sum is
+// sum_m B_m / x^(m+1), B_m = sum over lines and nodes of
+// s_j W_k / (sqrt(pi) beta_j) Im(z^m): the coefficients are taken lane-parallel
+// (lane j, line j) and summed over the warp, then every bin costs one
+// reciprocal and a Horner sum for the whole round.  Two forms:
+// * four nodes, 12 terms, over every bin of [gA + 1, gB - 1] outside U8 (the
+//   union of the lines' r2 < 64 bins): where every line has y <= 1.2 and
+//   |d_j| <= 0.2, |x| >= ~7.7 there and the terms after z^12 stay below
+//   1e-8 of the sum (8e-9 against the direct four-node sums in FP64 over
+//   seeded rounds); the batches keep only their edge groups, and their core
+//   and ring passes take the round's unions U and U8.
+// * two nodes (t = 1/sqrt 2, W = 1/2), 7 terms, over the two-node interiors
+//   [gA + 1, min L4 - 1] and [max R4 + 1, gB - 1] of the round: where every
+//   |z| <= 3 (|x| >= ~47 in the two-node band, terms after z^7 below 3.5e-8;
+//   5e-9 against the direct two-node sums in FP64).
+constexpr int KMP2 = 7, KMP4 = 12;   // series terms
 constexpr float kTnode = 0.70710678118654752f;
+constexpr float kT4a = 0.52464762327529031f, kT4b = 1.6506801238857845f;   // sqrt(tau_a, tau_b)
 
+// The series' parameters, written by lane 0 into the warp's queue rows (free
+// until the batches run: a round with a series has no per-line fallback).
 struct RoundSeries {
-    float B[KMP + 1];   // B[1..KMP]
+    float B[KMP4 + 1];   // B[1..K]
     float b0, nrb0, H;
-    int c0, RA, RB;     // the series covers groups [gA + 1, RA - 1] and [RB + 1, gB - 1]
-                        //   (disjoint: RA <= RB + 1)
-    bool on;
+    int c0, gA, gB;
+    int RA, RB;          // two nodes: the series covers [gA + 1, RA - 1] and [RB + 1, gB - 1]
+    int ulo, uhi, u8lo, u8hi;   // four nodes: the round's U and U8
 };
+static_assert(sizeof(RoundSeries) <= QCAP * sizeof(unsigned), "the series fits the queue rows");
 
-// Decides whether the round takes the series and, if so, its coefficients.
-// q: this lane's record (line `lane` of the round).  Called by the whole warp.
+// Decides whether the round takes a series and takes its coefficients.  q:
+// this lane's record (line `lane` of the round), before the batch summary.
+// Called by the whole warp.
 template <int V>
-__device__ __forceinline__ void round_series(const Rec &q, int lane, RoundSeries &rs)
+__device__ __forceinline__ int round_series(const Rec &q, int lane, RoundSeries &rs)
 {
     constexpr unsigned FULL = 0xffffffffu;
-    rs.on = false;
     const int c0 = __shfl_sync(FULL, q.c, 0), gA = __shfl_sync(FULL, q.gA, 0),
               gB = __shfl_sync(FULL, q.gB, 0);
     const float b0 = __shfl_sync(FULL, q.b, 0), rn0 = __shfl_sync(FULL, q.rn, 0);
@@ -739,73 +748,110 @@ __device__ __forceinline__ void round_series(const Rec &q, int lane, RoundSeries
         mL4 = min(mL4, __shfl_xor_sync(FULL, mL4, o));
         MR4 = max(MR4, __shfl_xor_sync(FULL, MR4, o));
     }
-    // this line's two nodes
     const float beta = q.b / b0;
     const float ib = 1.0f / beta;
     const float d = (rn0 - q.rn) * q.b;
-    const float ap = (kTnode - d) * ib, am = (-kTnode - d) * ib, cc = q.y * ib;
-    const float c2 = cc * cc;
-    const bool ok = (c0 == q.c) & (gA == q.gA) & (gB == q.gB) & (gA <= gB) &
-                    (fmaf(ap, ap, c2) <= 9.0f) & (fmaf(am, am, c2) <= 9.0f) &
-                    (mL4 > MR4 || (mL4 > gA && MR4 < gB));
-    if (!__all_sync(FULL, ok)) return;   // warp-uniform
-    const float wt = q.s * (float)(0.5 * kInvSqrtPi) * ib;
-    float B[KMP + 1];
-    B[0] = 0.0f;
+    const float cc = q.y * ib, c2 = cc * cc;
+    const float ap = (kTnode - d) * ib, am = (-kTnode - d) * ib;
+    const bool base = (c0 == q.c) & (gA == q.gA) & (gB == q.gB) & (gA <= gB) &
+                      (mL4 > MR4 || (mL4 > gA && MR4 < gB));
+    const bool ok4 = base & (q.y <= 1.2f) & (fabsf(d) <= 0.2f);
+    const bool ok2 = base & (fmaf(ap, ap, c2) <= 9.0f) & (fmaf(am, am, c2) <= 9.0f);
+    const int mode = __all_sync(FULL, ok4) ? 4 : (__all_sync(FULL, ok2) ? 2 : 0);
+    if (mode == 0) return 0;   // warp-uniform
+    const float ws = q.s * (float)kInvSqrtPi * ib;   // s / (sqrt(pi) beta), times W per node
+    float B[KMP4 + 1];
 #pragma unroll
-    for (int k = 1; k <= KMP; ++k) B[k] = 0.0f;
-#pragma unroll
-    for (int sgn = 0; sgn < 2; ++sgn) {
-        const float a = sgn ? am : ap;
+    for (int k = 0; k <= KMP4; ++k) B[k] = 0.0f;
+    auto pole = [&](float a, float wt, int K) {
         float zr = a, zi = cc;
 #pragma unroll
-        for (int k = 1; k <= KMP; ++k) {
+        for (int k = 1; k <= KMP4; ++k) {
+            if (k > K) break;
             B[k] = fmaf(wt, zi, B[k]);
             const float nr = fmaf(zr, a, -zi * cc), ni = fmaf(zr, cc, zi * a);
             zr = nr;
             zi = ni;
         }
+    };
+    if (mode == 4) {
+        const float wa = ws * (float)kWa * 0.5f, wb = ws * (float)kWb * 0.5f;
+        pole((kT4a - d) * ib, wa, KMP4);
+        pole((-kT4a - d) * ib, wa, KMP4);
+        pole((kT4b - d) * ib, wb, KMP4);
+        pole((-kT4b - d) * ib, wb, KMP4);
+    } else {
+        pole(ap, 0.5f * ws, KMP2);
+        pole(am, 0.5f * ws, KMP2);
     }
     float H = (V & kVPlinth) ? q.h : 0.0f;
+    const int K = mode == 4 ? KMP4 : KMP2;
+    // the round's U and U8 (four nodes): unions of the lines' [cl, ch] and [Lc, Rc]
+    int ul = q.cl <= q.ch ? q.cl : INT_MAX, uh = q.cl <= q.ch ? q.ch : INT_MIN;
+    int vl = q.Lc <= q.Rc ? q.Lc : INT_MAX, vh = q.Lc <= q.Rc ? q.Rc : INT_MIN;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int k = 1; k <= KMP; ++k) B[k] += __shfl_xor_sync(FULL, B[k], o);
+        for (int k = 1; k <= KMP4; ++k)
+            if (k <= K) B[k] += __shfl_xor_sync(FULL, B[k], o);
         if (V & kVPlinth) H += __shfl_xor_sync(FULL, H, o);
+        if (mode == 4) {
+            ul = min(ul, __shfl_xor_sync(FULL, ul, o));
+            uh = max(uh, __shfl_xor_sync(FULL, uh, o));
+            vl = min(vl, __shfl_xor_sync(FULL, vl, o));
+            vh = max(vh, __shfl_xor_sync(FULL, vh, o));
+        }
     }
+    if (lane == 0) {
 #pragma unroll
-    for (int k = 0; k <= KMP; ++k) rs.B[k] = B[k];
-    rs.b0 = b0;
-    rs.nrb0 = -rn0 * b0;
-    rs.H = H;
-    rs.c0 = c0;
-    if (mL4 <= MR4) {
-        rs.RA = mL4;
-        rs.RB = MR4;
-    } else {   // no four-node band in the round: all of [gA + 1, gB - 1] on the left
-        rs.RA = gB;
-        rs.RB = gB - 1;
+        for (int k = 0; k <= KMP4; ++k) rs.B[k] = B[k];
+        rs.b0 = b0;
+        rs.nrb0 = -rn0 * b0;
+        rs.H = H;
+        rs.c0 = c0;
+        rs.gA = gA;
+        rs.gB = gB;
+        rs.ulo = ul;
+        rs.uhi = uh;
+        rs.u8lo = vl;
+        rs.u8hi = vh;
+        if (mode == 4 || mL4 > MR4) {   // all of [gA + 1, gB - 1] on the left
+            rs.RA = gB;
+            rs.RB = gB - 1;
+        } else {
+            rs.RA = mL4;
+            rs.RB = MR4;
+        }
     }
-    rs.on = true;
+    __syncwarp();
+    return mode;
 }
 
-// The series over groups [g0, g1] of the tile (p: the warp's tile copy at g0).
+// The series (K terms) over groups [g0, g1] of the tile (p: the warp's tile
+// copy at g0); with `mask`, bins in [mlo, mhi] are left out.
+template <int K>
 __device__ __forceinline__ void round_sweep(const RoundSeries &rs, int g0, int g1, int tg0,
-                                            int tg1, float *base, int lane)
+                                            int tg1, float *base, int lane, int mlo, int mhi)
 {
     g0 = max(g0, tg0);
     g1 = min(g1, tg1);
     if (g0 > g1) return;
+    const unsigned mspan = (unsigned)(mhi - mlo);
+    float B[K + 1];
+#pragma unroll
+    for (int k = 1; k <= K; ++k) B[k] = rs.B[k];
+    const float b0 = rs.b0, nrb0 = rs.nrb0, H = rs.H;
     float kf = (float)(32 * g0 + lane - rs.c0);
+    int bin = 32 * g0 + lane;
     float *p = base + 32 * (g0 - tg0);
     float *const pe = base + 32 * (g1 - tg0);
-    for (; p <= pe; p += 32, kf += 32.0f) {
-        const float x = fmaf(kf, rs.b0, rs.nrb0);
+    for (; p <= pe; p += 32, kf += 32.0f, bin += 32) {
+        const float x = fmaf(kf, b0, nrb0);
         const float w = rcp_ftz(x);
-        float h = rs.B[KMP];
+        float h = B[K];
 #pragma unroll
-        for (int k = KMP - 1; k >= 1; --k) h = fmaf(h, w, rs.B[k]);
-        p[0] += fmaf(h, w * w, -rs.H);
+        for (int k = K - 1; k >= 1; --k) h = fmaf(h, w, B[k]);
+        if ((unsigned)(bin - mlo) > mspan) p[0] += fmaf(h, w * w, -H);
     }
 }
 
@@ -814,7 +860,7 @@ __device__ __forceinline__ void round_sweep(const RoundSeries &rs, int g0, int g
 template <int V, int NB>
 __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0, int tg1,
                                              float *base, int lane, unsigned *queue, int &qn,
-                                             int t0, int RA, int RB)
+                                             int t0, int RA, int RB, bool edges_only)
 {
     constexpr unsigned kAll = (1u << NB) - 1u;
     const Rec *R = &S.rec[warp][j0];
@@ -895,6 +941,7 @@ __device__ __forceinline__ unsigned do_batch(Smem &S, int warp, int j0, int tg0,
     edge(gA);
     if (gB == gA) return kAll;
     edge(gB);
+    if (edges_only) return kAll;   // warp-uniform: the round's four-node series took the rest
     // (the round's series covers [gA + 1, RA - 1] and [RB + 1, gB - 1]; with no
     // series RA = gA + 1 and RB = gB - 1, which cover nothing)
     if (!central) {
@@ -1305,26 +1352,41 @@ __global__ void __launch_bounds__(NT, 3)
                 q.R4 = q.ch = q.Rc = 0;
                 q.pad = 0.0f;
             }
-            if ((V & ~kVPlinth) == 0) batch_summary(q, lane);
+            // short lines: the round's series, when it can take one (before the
+            // batch summary, which overwrites fields of the batches' first records)
+            RoundSeries &rs = *reinterpret_cast<RoundSeries *>(S.queue[warp]);
+            int mode = 0;
+            if ((V & ~kVPlinth) == 0) {
+                mode = round_series<V>(q, lane, rs);
+                batch_summary(q, lane);
+                if (mode == 4) {   // the batches' core and ring passes take the round's U, U8
+                    if ((lane & (NLS - 1)) == 0) {
+                        q.L2 = rs.ulo;
+                        q.R2 = rs.uhi;
+                    } else if ((lane & (NLS - 1)) == 1) {
+                        q.Lc = rs.u8lo;
+                        q.Rc = rs.u8hi;
+                    }
+                }
+            }
             S.rec[warp][lane] = q;
             __syncwarp();
             int qn = 0;
             if ((V & ~kVPlinth) == 0) {   // short Voigt lines, with or without the plinth
-                // the round's two-node interiors as one series, when it can take it
-                RoundSeries rs;
-                round_series<V>(q, lane, rs);
                 int RA = INT_MIN, RB = INT_MAX;
-                if (rs.on) {   // warp-uniform
-                    const int gA = S.rec[warp][0].gA, gB = S.rec[warp][0].gB;
-                    round_sweep(rs, gA + 1, rs.RA - 1, tg0, tg1, accb, lane);
-                    round_sweep(rs, rs.RB + 1, gB - 1, tg0, tg1, accb, lane);
+                if (mode == 4) {   // warp-uniform
+                    round_sweep<KMP4>(rs, rs.gA + 1, rs.gB - 1, tg0, tg1, accb, lane, rs.u8lo,
+                                      rs.u8lo <= rs.u8hi ? rs.u8hi : rs.u8lo - 1);
+                } else if (mode == 2) {
+                    round_sweep<KMP2>(rs, rs.gA + 1, rs.RA - 1, tg0, tg1, accb, lane, 1, 0);
+                    round_sweep<KMP2>(rs, rs.RB + 1, rs.gB - 1, tg0, tg1, accb, lane, 1, 0);
                     RA = rs.RA;
                     RB = rs.RB;
                 }
                 unsigned rmask = 0u;
                 for (int j0 = 0; j0 < 32; j0 += NLS)
                     rmask |= do_batch<V, NLS>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0,
-                                              RA, RB)
+                                              RA, RB, mode == 4)
                              << j0;
                 drain_rest(queue, qn, S, warp, lane, t0, accb - lane);
                 core_slots<NLS, false>(S, warp, lane, rmask, t0, t1, accb - lane);
