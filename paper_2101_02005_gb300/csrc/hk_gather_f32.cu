@@ -1207,6 +1207,126 @@ __device__ __forceinline__ void wide_masked(const Rec *R, int g0, int g1, float 
     }
 }
 
+// ---- a wide round's far groups as one series in 1/x --------------------------
+//
+// Wide lines (the peeled Voigt instance): the 32 lines of a warp's round, all
+// inside their cut and outside their four-node groups over a stretch of the
+// tile -- left of every line's four-node groups, [max gA + 1, min L4 - 1], and
+// right of them, [max R4 + 1, min gB - 1] -- take the two-node rule there,
+// and their sum is the series of the short-line rounds (two Lorentzians per
+// line, expanded about line 0's offset x; d_j now includes the lines' whole
+// bin offsets).  It is used on the groups whose every bin has |x| >= 5 |z|max
+// (the terms after z^12 stay below 13 0.2^12 = 5.3e-8 of the sum) with 12
+// terms, and with the first 4 terms where |x| >= 100 |z|max (5 0.01^4 = 5e-8);
+// never when |z|max > 1000 (the powers' float range) or when line 0 has no
+// four-node band.  Returns the groups it covered, [cv[0], cv[1]] and
+// [cv[2], cv[3]] (empty: first > last), left for the batches to skip.
+constexpr int KW = 12, KWF = 4;
+
+template <int K>
+__device__ __forceinline__ void wide_series_sweep(const float *B, float b0, float nrb0, float H,
+                                                  int c0, int g0, int g1, int tg0, float *base,
+                                                  int lane)
+{
+    if (g0 > g1) return;
+    float kf = (float)(32 * g0 + lane - c0);
+    float *p = base + 32 * (g0 - tg0);
+    float *const pe = base + 32 * (g1 - tg0);
+    for (; p <= pe; p += 32, kf += 32.0f) {
+        const float x = fmaf(kf, b0, nrb0);
+        const float w = rcp_ftz(x);
+        float h = B[K];
+#pragma unroll
+        for (int k = K - 1; k >= 1; --k) h = fmaf(h, w, B[k]);
+        p[0] += fmaf(h, w * w, -H);
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void wide_round(const Rec &q, bool valid, int lane, int tg0, int tg1,
+                                           float *base, int *cv)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    cv[0] = cv[2] = 1;
+    cv[1] = cv[3] = 0;
+    const bool has4 = q.L4 <= q.R4;
+    const int c0 = __shfl_sync(FULL, q.c, 0);
+    const float b0 = __shfl_sync(FULL, q.b, 0), rn0 = __shfl_sync(FULL, q.rn, 0);
+    const bool has40 = __shfl_sync(FULL, has4 ? 1 : 0, 0) != 0;
+    // this line's two nodes about line 0's offset
+    const float beta = q.b / b0;
+    const float ib = 1.0f / beta;
+    const float d = ((float)(c0 - q.c) + (rn0 - q.rn)) * q.b;
+    const float cc = q.y * ib;
+    const float ap = (kTnode - d) * ib, am = (-kTnode - d) * ib;
+    float zm = sqrtf(fmaxf(fmaf(ap, ap, cc * cc), fmaf(am, am, cc * cc)));
+    // the safe stretches: inside every cut, outside every line's four-node groups
+    int aL = q.gA + 1, bL = has4 ? q.L4 - 1 : q.gB - 1;
+    int aR = has4 ? q.R4 + 1 : q.gA + 1, bR = q.gB - 1;
+    int any4 = has4 ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        zm = fmaxf(zm, __shfl_xor_sync(FULL, zm, o));
+        aL = max(aL, __shfl_xor_sync(FULL, aL, o));
+        bL = min(bL, __shfl_xor_sync(FULL, bL, o));
+        aR = max(aR, __shfl_xor_sync(FULL, aR, o));
+        bR = min(bR, __shfl_xor_sync(FULL, bR, o));
+        any4 |= __shfl_xor_sync(FULL, any4, o);
+    }
+    const bool ok = valid && q.gA <= q.gB;
+    if (!__all_sync(FULL, ok) || !has40 || !(zm <= 1000.0f)) return;   // warp-uniform
+    // groups whose every bin is at least X from the reference centre c0 + rn0
+    const float cen = (float)c0 + rn0;
+    auto left_of = [&](float X) { return (int)floorf((cen - X / b0 - 31.0f) * (1.0f / 32.0f)); };
+    auto right_of = [&](float X) { return (int)ceilf((cen + X / b0) * (1.0f / 32.0f)); };
+    const int gl = left_of(5.0f * zm), gr = right_of(5.0f * zm);
+    const int gl4 = left_of(100.0f * zm), gr4 = right_of(100.0f * zm);
+    // left cover [l0, l1], right cover [r0, r1] (both clear of line 0's centre)
+    const int l0 = max(aL, tg0), l1 = min(min(bL, gl), tg1);
+    const int r0 = max(max(aR, gr), tg0), r1 = min(bR, tg1);
+    const bool useL = l0 <= l1, useR = r0 <= r1 && any4;
+    if (!useL && !useR) return;
+    // coefficients: lane j, line j; summed over the warp
+    const float wt = q.s * (float)(0.5 * kInvSqrtPi) * ib;
+    float B[KW + 1];
+#pragma unroll
+    for (int k = 0; k <= KW; ++k) B[k] = 0.0f;
+#pragma unroll
+    for (int sgn = 0; sgn < 2; ++sgn) {
+        const float a = sgn ? am : ap;
+        float zr = a, zi = cc;
+#pragma unroll
+        for (int k = 1; k <= KW; ++k) {
+            B[k] = fmaf(wt, zi, B[k]);
+            const float nr = fmaf(zr, a, -zi * cc), ni = fmaf(zr, cc, zi * a);
+            zr = nr;
+            zi = ni;
+        }
+    }
+    float H = (V & kVPlinth) ? q.h : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 1; k <= KW; ++k) B[k] += __shfl_xor_sync(FULL, B[k], o);
+        if (V & kVPlinth) H += __shfl_xor_sync(FULL, H, o);
+    }
+    const float nrb0 = -rn0 * b0;
+    if (useL) {   // far part (4 terms) then near part (12 terms)
+        const int m = min(l1, gl4);
+        wide_series_sweep<KWF>(B, b0, nrb0, H, c0, l0, m, tg0, base, lane);
+        wide_series_sweep<KW>(B, b0, nrb0, H, c0, max(l0, m + 1), l1, tg0, base, lane);
+        cv[0] = l0;
+        cv[1] = l1;
+    }
+    if (useR) {
+        const int m = max(r0, gr4);
+        wide_series_sweep<KW>(B, b0, nrb0, H, c0, r0, m - 1 < r1 ? m - 1 : r1, tg0, base, lane);
+        wide_series_sweep<KWF>(B, b0, nrb0, H, c0, m, r1, tg0, base, lane);
+        cv[2] = r0;
+        cv[3] = r1;
+    }
+}
+
 // Batches of wide lines (the peeled instances: Voigt and Lorentzian, with or
 // without the plinth).  The lines of a batch have their own centres; their
 // per-tile flags (wide_flags) decide the tile's handling:
@@ -1221,7 +1341,7 @@ __device__ __forceinline__ void wide_masked(const Rec *R, int g0, int g1, float 
 template <int V>
 __device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0, int tg1,
                                               float *base, int lane, unsigned *queue, int &qn,
-                                              int t0)
+                                              int t0, int rg0, int rg1)
 {
     const Rec *R = &S.rec[warp][j0];
     int fand = 127, fany = 0, cls = -1;
@@ -1240,15 +1360,15 @@ __device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0
     const bool edges = cls == 0;
     // masked spans of at most kMaskSpan groups in all: the masked rule takes
     // every line in every group of a span, whether the line has bins there or not
-    const int span = max(min(A1, tg1) - max(A0, tg0) + 1, 0) + max(min(B1, tg1) - max(B0, tg0) + 1, 0);
+    const int span = max(min(A1, rg1) - max(A0, rg0) + 1, 0) + max(min(B1, rg1) - max(B0, rg0) + 1, 0);
     if (edges && !((fand & 16) && !(fany & 64) && A1 < B0 && span <= kMaskSpan)) {
         for (int j = 0; j < NLB; ++j) {
             const Rec q = S.rec[warp][j0 + j];
-            do_line<V>(q, j0 + j, tg0, tg1, base, lane, queue, qn, S, warp, t0, tg0, tg1);
+            do_line<V>(q, j0 + j, tg0, tg1, base, lane, queue, qn, S, warp, t0, rg0, rg1);
         }
         return;
     }
-    const int g0 = edges ? max(A1 + 1, tg0) : tg0, g1 = edges ? min(B0 - 1, tg1) : tg1;
+    const int g0 = edges ? max(A1 + 1, rg0) : rg0, g1 = edges ? min(B0 - 1, rg1) : rg1;
     if (g0 <= g1)
         wide_sweep<V>(R, edges ? 2 : cls, (fand & (edges ? 32 : 4)) != 0, !edges && (fand & 8),
                       g0, g1, base + 32 * (g0 - tg0), lane);
@@ -1262,7 +1382,7 @@ __device__ __forceinline__ void do_batch_wide(Smem &S, int warp, int j0, int tg0
             b1 = max(b1, R[j].gB);
         }
         for (int k = 0; k < 2; ++k) {
-            const int m0 = max(k ? b0 : a0, tg0), m1 = min(k ? b1 : a1, tg1);
+            const int m0 = max(k ? b0 : a0, rg0), m1 = min(k ? b1 : a1, rg1);
             if (m0 <= m1) wide_masked<V>(R, m0, m1, base + 32 * (m0 - tg0), lane);
         }
     }
@@ -1392,8 +1512,33 @@ __global__ void __launch_bounds__(NT, 3)
                 core_slots<NLS, false>(S, warp, lane, rmask, t0, t1, accb - lane);
                 core_slots<NLS, true>(S, warp, lane, rmask, t0, t1, accb - lane);
             } else if ((V & kVPeel) && !(V & (kVDoppler | kVBinned))) {
-                for (int j0 = 0; j0 < 32; j0 += NLB)
-                    do_batch_wide<V>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0);
+                // the round's far groups as one series (Voigt), then the batches on
+                // the rest of the tile
+                int cv[4] = {1, 0, 1, 0};
+                if (g.profile == kProfVoigt) wide_round<V>(q, l < l_end, lane, tg0, tg1, accb, cv);
+                int pr0[3], pr1[3], np = 0, start = tg0;
+                if (cv[0] <= cv[1]) {
+                    if (start < cv[0]) {
+                        pr0[np] = start;
+                        pr1[np++] = cv[0] - 1;
+                    }
+                    start = cv[1] + 1;
+                }
+                if (cv[2] <= cv[3]) {
+                    if (start < cv[2]) {
+                        pr0[np] = start;
+                        pr1[np++] = cv[2] - 1;
+                    }
+                    start = cv[3] + 1;
+                }
+                if (start <= tg1) {
+                    pr0[np] = start;
+                    pr1[np++] = tg1;
+                }
+                for (int k = 0; k < np; ++k)
+                    for (int j0 = 0; j0 < 32; j0 += NLB)
+                        do_batch_wide<V>(S, warp, j0, tg0, tg1, accb, lane, queue, qn, t0, pr0[k],
+                                         pr1[k]);
             } else {
                 for (int j = 0; j < 32; ++j) {
                     // a register copy: the record must not be re-read from shared
