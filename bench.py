@@ -44,10 +44,10 @@ METRIC = "lines/s and Voigt evals/s on 1 GB300 (FP32-comp vs FP64 GPU) at stated
 # take out of the core count.
 FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 25, "gh4": 25, "ring8": 45, "core": 200}
 # DRAM bytes per line of one k_gather_f32 launch, from the ncu capture in
-# profiles/k_gather_f32_config1-1e7-lines.md (242.2 MB read + 3.5 MB written for
-# 1e7 lines; the line list is read once, so traffic grows with the line
+# profiles/k_gather_f32_config1-5e7-lines.md (1201.3 MB read + 4.7 MB written for
+# 5e7 lines; the line list is read once, so traffic grows with the line
 # count).  Set to None when the kernel changes.
-GATHER_DRAM_BYTES_PER_LINE = 24.57
+GATHER_DRAM_BYTES_PER_LINE = 24.12
 FP32_LANES_PER_SM = 128
 
 
@@ -709,9 +709,9 @@ def main():
         "kernel": ("k_gather_f32<0> (batched short-line sweeps)"
                    if 2 * w.cut / w.grid.dnu + 1 < 1024 else "k_gather_f32<1> (peeled sweeps)"),
         "traffic": traffic,
-        "traffic_basis": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 1e7-line "
-                          "launch of this kernel (profiles/k_gather_f32_config1-1e7-lines.md), "
-                          "24.6 B per line, scaled by the line count" if traffic else None),
+        "traffic_basis": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one 5e7-line "
+                          "launch of this kernel (profiles/k_gather_f32_config1-5e7-lines.md), "
+                          "24.1 B per line, scaled by the line count" if traffic else None),
         "algorithmic_bytes": 24 * L.n, "gather_ms_per_launch": g_ms,
         "gather_share_of_step": g_ms / ms_step if ms_step else None,
         "flops_per_step": flops_step, "cost_model": FLOPS_PER_PAIR,
