@@ -1,0 +1,168 @@
+"""The accuracy claims of the FP32C kernel's batch rules, checked in FP64 on the
+CPU (no GPU): the 8-node Gauss-Hermite ring of the short-line core, and the
+series in 1/x that sums a warp's 32 lines at once (two-node form over the
+short-line interiors, four-node form over everything outside the r2 < 64
+union, the wide-line form with 12 and 4 terms).  Each rule is written here
+from its definition -- Gauss-Hermite nodes from numpy, the Lorentzian
+expansion 1/((x-a)^2 + c^2) = Im(1/(x - z))/c, 1/(x - z) = sum z^m / x^(m+1)
+-- and compared with the direct sums (scipy's wofz for the ring), on seeded
+rounds built like the kernel's, with the bounds the kernel uses to choose
+them.  The GPU parity tests compare the kernel itself with the oracle."""
+import numpy as np
+import pytest
+
+scipy_special = pytest.importorskip("scipy.special")
+
+SQPI = np.sqrt(np.pi)
+
+
+def gh_pairs(n):
+    """Positive Gauss-Hermite nodes t_k of an n-node rule and the normalised
+    weights of the node pairs (sum of all weights 1)."""
+    t, w = np.polynomial.hermite.hermgauss(n)
+    w = w / SQPI
+    keep = t > 0
+    return t[keep], 2.0 * w[keep]
+
+
+def ring_r2(y):
+    return np.minimum(64.0, np.maximum(26.0, np.log(1.13e9) - np.log(y)))
+
+
+def test_ring_rule_meets_its_bound():
+    """8 nodes over R8(y) <= r2 < 64: within 2e-7 of Re w (y from 1e-9 to 8)."""
+    t, W = gh_pairs(8)
+    rng = np.random.default_rng(11)
+    y = np.concatenate([10 ** rng.uniform(-9, np.log10(8), 200000), rng.uniform(0, 8, 100000)])
+    R = ring_r2(y)
+    r2 = R + rng.uniform(0, 1, y.size) * (64.0 - R)
+    ok = (r2 < 64.0) & (r2 > y * y)
+    y, r2 = y[ok], r2[ok]
+    x = np.sqrt(r2 - y * y)
+    X, Y = x * x, y * y
+    F = sum(Wj * (r2 + tj * tj) / ((X - Y - tj * tj) ** 2 + 4 * X * Y) for tj, Wj in zip(t, W))
+    got = y / SQPI * F
+    ref = scipy_special.wofz(x + 1j * y).real
+    assert np.max(np.abs(got - ref) / ref) <= 2e-7
+
+
+def lorentz_direct(bins, lines, nodes):
+    """sum over lines and nodes of s W / (sqrt(pi)) * y / ((x_j - t)^2 + y^2),
+    x_j = (bin - centre_j) b_j: the lines' Gauss-Hermite values."""
+    v = np.zeros(bins.size)
+    for b, cen, y, s in lines:
+        x = (bins - cen) * b
+        for t, W in nodes:
+            v += s * y / SQPI * W / ((x - t) ** 2 + y * y)
+    return v
+
+
+def series(bins, lines, nodes, K, kuse=None):
+    """The round's series about line 0: B_m = sum s W Im(z^m) / (sqrt(pi) beta),
+    z = ((t - d) + i y) / beta, evaluated as sum_m B_m / x^(m+1)."""
+    b0, c0 = lines[0][0], lines[0][1]
+    B = np.zeros(K + 1)
+    zmax = 0.0
+    for b, cen, y, s in lines:
+        beta = b / b0
+        d = (c0 - cen) * b
+        for t, W in nodes:
+            z = complex((t - d) / beta, y / beta)
+            zmax = max(zmax, abs(z))
+            zk = 1.0 + 0j
+            for m in range(1, K + 1):
+                zk *= z
+                B[m] += s * W / (SQPI * beta) * zk.imag
+    k = kuse or K
+    x = (bins - c0) * b0
+    w = 1.0 / x
+    h = np.full(x.size, B[k])
+    for m in range(k - 1, 0, -1):
+        h = h * w + B[m]
+    return h * w * w, zmax
+
+
+def two_nodes():
+    t = 1.0 / np.sqrt(2.0)
+    return [(t, 0.5), (-t, 0.5)]
+
+
+def four_nodes():
+    t, W = gh_pairs(4)
+    return [(tj, Wj / 2) for tj, Wj in zip(t, W)] + [(-tj, Wj / 2) for tj, Wj in zip(t, W)]
+
+
+def short_round(rng, spread, ymax):
+    b0 = rng.uniform(0.8, 3.0)
+    c0 = rng.uniform(-0.5, 0.5)
+    return [(b0 * (1 + rng.uniform(-2e-7, 2e-7)), c0 + rng.uniform(-spread, spread),
+             10 ** rng.uniform(-4, np.log10(ymax)), 10 ** rng.uniform(-3, 0)) for _ in range(32)]
+
+
+def test_two_node_round_series():
+    """7 terms over the two-node band (every line's r2 >= 2500) when |z| <= 3."""
+    rng = np.random.default_rng(12)
+    worst, used = 0.0, 0
+    for _ in range(300):
+        lines = short_round(rng, 0.5, 2.2)
+        bins = lines[0][1] + np.concatenate([np.arange(-300, -10), np.arange(10, 300)])
+        ok = np.ones(bins.size, bool)
+        for b, cen, y, s in lines:
+            ok &= ((bins - cen) * b) ** 2 + y * y >= 2500.0
+        got, zmax = series(bins[ok], lines, two_nodes(), 7)
+        if zmax > 3.0 or not ok.any():
+            continue
+        used += 1
+        ref = lorentz_direct(bins[ok], lines, two_nodes())
+        worst = max(worst, np.max(np.abs(got - ref) / ref))
+    assert used > 100 and worst <= 1e-7
+
+
+def test_four_node_round_series():
+    """12 terms over every bin where each line has r2 >= 64, lines with
+    y <= 1.2 and offsets |d| <= 0.2."""
+    rng = np.random.default_rng(13)
+    worst = 0.0
+    for _ in range(300):
+        b0 = rng.uniform(0.8, 3.0)
+        lines = [(b0 * (1 + rng.uniform(-2e-7, 2e-7)), rng.uniform(-0.2, 0.2) / b0,
+                  10 ** rng.uniform(-4, np.log10(1.2)), 10 ** rng.uniform(-3, 0))
+                 for _ in range(32)]
+        bins = np.arange(-300, 301, dtype=float)
+        ok = np.ones(bins.size, bool)
+        for b, cen, y, s in lines:
+            ok &= ((bins - cen) * b) ** 2 + y * y >= 64.0
+        got, _ = series(bins[ok], lines, four_nodes(), 12)
+        ref = lorentz_direct(bins[ok], lines, four_nodes())
+        worst = max(worst, np.max(np.abs(got - ref) / ref))
+    assert worst <= 1e-7
+
+
+def test_wide_round_series():
+    """Wide lines: 12 terms where |x| >= 5 |z|max, 4 terms where |x| >= 100
+    |z|max, centre offsets up to 300 bins, every line in its two-node band."""
+    rng = np.random.default_rng(14)
+    worst = {12: 0.0, 4: 0.0}
+    for _ in range(200):
+        b0 = rng.uniform(0.1, 3.0)
+        c0 = rng.uniform(0, 1)
+        span = rng.choice([2, 25, 300])
+        lines = [(b0 * (1 + rng.uniform(-1e-3, 1e-3)) if j else b0,
+                  c0 + (rng.uniform(-span, span) if j else 0.0),
+                  10 ** rng.uniform(-6, 1.5), 10 ** rng.uniform(-3, 0)) for j in range(32)]
+        _, zmax = series(np.array([1e9]), lines, two_nodes(), 12)
+        if zmax > 1000.0:
+            continue
+        for lo, hi, K in [(5, 100, 12), (100, 3000, 4)]:
+            xs = np.concatenate([np.linspace(lo * zmax, hi * zmax, 200),
+                                 -np.linspace(lo * zmax, hi * zmax, 200)])
+            bins = c0 + xs / b0
+            ok = np.ones(bins.size, bool)
+            for b, cen, y, s in lines:
+                ok &= ((bins - cen) * b) ** 2 + y * y >= 2500.0
+            if not ok.any():
+                continue
+            got, _ = series(bins[ok], lines, two_nodes(), 12, K)
+            ref = lorentz_direct(bins[ok], lines, two_nodes())
+            worst[K] = max(worst[K], np.max(np.abs(got - ref) / ref))
+    assert worst[12] <= 1e-7 and worst[4] <= 1e-7, worst
