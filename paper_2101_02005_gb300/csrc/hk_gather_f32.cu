@@ -715,7 +715,8 @@ __device__ __forceinline__ void batch_summary(Rec &q, int lane)
 // * two nodes (t = 1/sqrt 2, W = 1/2), 7 terms, over the two-node interiors
 //   [gA + 1, min L4 - 1] and [max R4 + 1, gB - 1] of the round: where every
 //   |z| <= 3 (|x| >= ~47 in the two-node band, terms after z^7 below 3.5e-8;
-//   5e-9 against the direct two-node sums in FP64).
+//   5e-9 against the direct two-node sums in FP64); with 12 terms where every
+//   |z| <= 7 (terms after z^12 below 13 (7/47)^12 = 1e-9).
 constexpr int KMP2 = 7, KMP4 = 12;   // series terms
 constexpr float kTnode = 0.70710678118654752f;
 constexpr float kT4a = 0.52464762327529031f, kT4b = 1.6506801238857845f;   // sqrt(tau_a, tau_b)
@@ -756,8 +757,11 @@ __device__ __forceinline__ int round_series(const Rec &q, int lane, RoundSeries 
     const bool base = (c0 == q.c) & (gA == q.gA) & (gB == q.gB) & (gA <= gB) &
                       (mL4 > MR4 || (mL4 > gA && MR4 < gB));
     const bool ok4 = base & (q.y <= 1.2f) & (fabsf(d) <= 0.2f);
-    const bool ok2 = base & (fmaf(ap, ap, c2) <= 9.0f) & (fmaf(am, am, c2) <= 9.0f);
-    const int mode = __all_sync(FULL, ok4) ? 4 : (__all_sync(FULL, ok2) ? 2 : 0);
+    const float zz = fmaxf(fmaf(ap, ap, c2), fmaf(am, am, c2));
+    const bool ok2 = base & (zz <= 9.0f), ok3 = base & (zz <= 49.0f);
+    // 4: four nodes; 2: two nodes, 7 terms; 3: two nodes, 12 terms
+    const int mode = __all_sync(FULL, ok4) ? 4
+                     : (__all_sync(FULL, ok2) ? 2 : (__all_sync(FULL, ok3) ? 3 : 0));
     if (mode == 0) return 0;   // warp-uniform
     const float ws = q.s * (float)kInvSqrtPi * ib;   // s / (sqrt(pi) beta), times W per node
     float B[KMP4 + 1];
@@ -781,11 +785,11 @@ __device__ __forceinline__ int round_series(const Rec &q, int lane, RoundSeries 
         pole((kT4b - d) * ib, wb, KMP4);
         pole((-kT4b - d) * ib, wb, KMP4);
     } else {
-        pole(ap, 0.5f * ws, KMP2);
-        pole(am, 0.5f * ws, KMP2);
+        pole(ap, 0.5f * ws, mode == 3 ? KMP4 : KMP2);
+        pole(am, 0.5f * ws, mode == 3 ? KMP4 : KMP2);
     }
     float H = (V & kVPlinth) ? q.h : 0.0f;
-    const int K = mode == 4 ? KMP4 : KMP2;
+    const int K = mode == 2 ? KMP2 : KMP4;
     // the round's U and U8 (four nodes): unions of the lines' [cl, ch] and [Lc, Rc]
     int ul = q.cl <= q.ch ? q.cl : INT_MAX, uh = q.cl <= q.ch ? q.ch : INT_MIN;
     int vl = q.Lc <= q.Rc ? q.Lc : INT_MAX, vh = q.Lc <= q.Rc ? q.Rc : INT_MIN;
@@ -1500,6 +1504,11 @@ __global__ void __launch_bounds__(NT, 3)
                 } else if (mode == 2) {
                     round_sweep<KMP2>(rs, rs.gA + 1, rs.RA - 1, tg0, tg1, accb, lane, 1, 0);
                     round_sweep<KMP2>(rs, rs.RB + 1, rs.gB - 1, tg0, tg1, accb, lane, 1, 0);
+                    RA = rs.RA;
+                    RB = rs.RB;
+                } else if (mode == 3) {
+                    round_sweep<KMP4>(rs, rs.gA + 1, rs.RA - 1, tg0, tg1, accb, lane, 1, 0);
+                    round_sweep<KMP4>(rs, rs.RB + 1, rs.gB - 1, tg0, tg1, accb, lane, 1, 0);
                     RA = rs.RA;
                     RB = rs.RB;
                 }

@@ -118,6 +118,25 @@ def test_two_node_round_series():
     assert used > 100 and worst <= 1e-7
 
 
+def test_two_node_round_series_twelve_terms():
+    """12 terms over the two-node band when 3 < |z| <= 7 (larger y)."""
+    rng = np.random.default_rng(15)
+    worst, used = 0.0, 0
+    for _ in range(300):
+        lines = short_round(rng, 0.5, 6.5)
+        bins = lines[0][1] + np.concatenate([np.arange(-300, -10), np.arange(10, 300)])
+        ok = np.ones(bins.size, bool)
+        for b, cen, y, s in lines:
+            ok &= ((bins - cen) * b) ** 2 + y * y >= 2500.0
+        got, zmax = series(bins[ok], lines, two_nodes(), 12)
+        if zmax > 7.0 or zmax <= 3.0 or not ok.any():
+            continue
+        used += 1
+        ref = lorentz_direct(bins[ok], lines, two_nodes())
+        worst = max(worst, np.max(np.abs(got - ref) / ref))
+    assert used > 100 and worst <= 1e-7
+
+
 def test_four_node_round_series():
     """12 terms over every bin where each line has r2 >= 64, lines with
     y <= 1.2 and offsets |d| <= 0.2."""
