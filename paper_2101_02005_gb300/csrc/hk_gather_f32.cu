@@ -718,6 +718,7 @@ __device__ __forceinline__ void batch_summary(Rec &q, int lane)
 //   5e-9 against the direct two-node sums in FP64); with 12 terms where every
 //   |z| <= 7 (terms after z^12 below 13 (7/47)^12 = 1e-9).
 constexpr int KMP2 = 7, KMP4 = 12;   // series terms
+constexpr int kNoBin = 0x3fffffff;   // a bin index no grid reaches
 constexpr float kTnode = 0.70710678118654752f;
 constexpr float kT4a = 0.52464762327529031f, kT4b = 1.6506801238857845f;   // sqrt(tau_a, tau_b)
 
@@ -832,7 +833,8 @@ __device__ __forceinline__ int round_series(const Rec &q, int lane, RoundSeries 
 }
 
 // The series (K terms) over groups [g0, g1] of the tile (p: the warp's tile
-// copy at g0); with `mask`, bins in [mlo, mhi] are left out.
+// copy at g0); bins in [mlo, mhi] are left out (mlo <= mhi; kNoBin, kNoBin
+// for none: no bin reaches it).
 template <int K>
 __device__ __forceinline__ void round_sweep(const RoundSeries &rs, int g0, int g1, int tg0,
                                             int tg1, float *base, int lane, int mlo, int mhi)
@@ -1499,16 +1501,21 @@ __global__ void __launch_bounds__(NT, 3)
             if ((V & ~kVPlinth) == 0) {   // short Voigt lines, with or without the plinth
                 int RA = INT_MIN, RB = INT_MAX;
                 if (mode == 4) {   // warp-uniform
-                    round_sweep<KMP4>(rs, rs.gA + 1, rs.gB - 1, tg0, tg1, accb, lane, rs.u8lo,
-                                      rs.u8lo <= rs.u8hi ? rs.u8hi : rs.u8lo - 1);
+                    const bool u8 = rs.u8lo <= rs.u8hi;
+                    round_sweep<KMP4>(rs, rs.gA + 1, rs.gB - 1, tg0, tg1, accb, lane,
+                                      u8 ? rs.u8lo : kNoBin, u8 ? rs.u8hi : kNoBin);
                 } else if (mode == 2) {
-                    round_sweep<KMP2>(rs, rs.gA + 1, rs.RA - 1, tg0, tg1, accb, lane, 1, 0);
-                    round_sweep<KMP2>(rs, rs.RB + 1, rs.gB - 1, tg0, tg1, accb, lane, 1, 0);
+                    round_sweep<KMP2>(rs, rs.gA + 1, rs.RA - 1, tg0, tg1, accb, lane, kNoBin,
+                                      kNoBin);
+                    round_sweep<KMP2>(rs, rs.RB + 1, rs.gB - 1, tg0, tg1, accb, lane, kNoBin,
+                                      kNoBin);
                     RA = rs.RA;
                     RB = rs.RB;
                 } else if (mode == 3) {
-                    round_sweep<KMP4>(rs, rs.gA + 1, rs.RA - 1, tg0, tg1, accb, lane, 1, 0);
-                    round_sweep<KMP4>(rs, rs.RB + 1, rs.gB - 1, tg0, tg1, accb, lane, 1, 0);
+                    round_sweep<KMP4>(rs, rs.gA + 1, rs.RA - 1, tg0, tg1, accb, lane, kNoBin,
+                                      kNoBin);
+                    round_sweep<KMP4>(rs, rs.RB + 1, rs.gB - 1, tg0, tg1, accb, lane, kNoBin,
+                                      kNoBin);
                     RA = rs.RA;
                     RB = rs.RB;
                 }

@@ -781,3 +781,62 @@ def test_ring_pair_count(hk):
     assert abs(ring - want) <= 1e-3 * want + 20, (ring, want)
     assert hk.hk_count_ring_pairs(D, g, st, hk.make_opts(QREF, w.cut, hk.HK_FP64)) == 0
     assert hk.hk_count_ring_pairs(D, g, st, hk.make_opts(QREF, 600.0)) == 0   # 12001 bins
+
+
+@pytest.mark.parametrize("plinth", [False, True])
+def test_round_series_parity(hk, plinth):
+    """Short lines in dense clusters of 128 lines within 0.02 bins of a bin
+    centre, so that whole 32-line rounds share their centre bin and take the
+    round series, with Lorentz widths chosen per cluster for each form: y near
+    0.4 (four nodes), 1.8 (two nodes, 7 terms), 5 (two nodes, 12 terms) and 21
+    (no series), at nu0 ~ 14500 cm^-1 (x step ~1.7 per bin, as at config 1);
+    modest strengths and lower-state energies keep the whole array above the
+    mask, so every bin is held to the bar.  FP32C against the oracle."""
+    rng = np.random.default_rng(31 + plinth)
+    dnu, nu_min, nbins = 0.1, 14000.0, 9000
+    nu0, gam = [], []
+    for i, k in enumerate(np.linspace(400, nbins - 400, 16).astype(int)):
+        base = nu_min + k * dnu
+        nu0.extend((base + np.sort(rng.uniform(-2e-3, 2e-3, 128))).tolist())
+        g = [0.05, 0.25, 0.7, 3.0][i % 4]
+        gam.extend((g * rng.uniform(0.85, 1.0, 128)).tolist())
+    nu0 = np.asarray(nu0)
+    n = nu0.size
+    L = synth.LineList(nu0, (10 ** rng.uniform(-22, -20, n)).astype(np.float32),
+                       rng.exponential(300.0, n).astype(np.float32),
+                       np.asarray(gam, np.float32), np.full(n, 0.5, np.float32), 18.0)
+    grid = synth.Grid(nu_min, dnu, nbins)
+    T, P = 1500.0, 1.0
+    flags = hk.HK_SIGMA_F64 | (hk.HK_REMOVE_PLINTH if plinth else 0)
+    got = gpu_sigma(hk, L, grid, T, P, 25.0, 0, flags=flags)
+    ref = oracle.cross_section(L.as_oracle(), grid.astuple(), (T, P, float(Q(T)), QREF), 25.0,
+                               plinth=plinth)
+    if plinth:
+        raw = oracle_sigma(L, grid, T, P, 25.0)
+        assert_plinth_close(got, ref, raw, "round series, plinth")
+    else:
+        assert_sigma_close(got, ref, "round series")
+        m = ref > 1e-10 * ref.max()
+        assert m.mean() > 0.5, m.mean()
+    assert np.array_equal(ref == 0, got == 0)
+
+
+def test_wide_round_series_parity(hk):
+    """Wide lines (cut 100 at 0.01 cm^-1: 20001 bins) packed ten to a bin, so
+    that a round's lines lie within a few bins and its far tiles take the
+    wide-line series; Lorentz widths from small to large.  FP32C against the
+    oracle over the whole array."""
+    rng = np.random.default_rng(41)
+    dnu, nu_min, nbins = 0.01, 14900.0, 30000
+    n = 6000
+    nu0 = np.sort(nu_min + (15000 + rng.uniform(-300, 300, n)) * dnu)
+    L = synth.LineList(nu0, (10 ** rng.uniform(-22, -20, n)).astype(np.float32),
+                       rng.exponential(300.0, n).astype(np.float32),
+                       (10 ** rng.uniform(-3, 0, n)).astype(np.float32),
+                       rng.uniform(0.3, 0.8, n).astype(np.float32), 18.0)
+    grid = synth.Grid(nu_min, dnu, nbins)
+    for T, P in [(1000.0, 0.1), (2000.0, 10.0)]:
+        got = gpu_sigma(hk, L, grid, T, P, 100.0, 0, flags=hk.HK_SIGMA_F64)
+        ref = oracle_sigma(L, grid, T, P, 100.0)
+        assert_sigma_close(got, ref, f"wide round series T={T} P={P}")
+        assert np.array_equal(ref == 0, got == 0), (T, P)
