@@ -7,13 +7,24 @@ from its definition -- Gauss-Hermite nodes from numpy, the Lorentzian
 expansion 1/((x-a)^2 + c^2) = Im(1/(x - z))/c, 1/(x - z) = sum z^m / x^(m+1)
 -- and compared with the direct sums (scipy's wofz for the ring), on seeded
 rounds built like the kernel's, with the bounds the kernel uses to choose
-them.  The GPU parity tests compare the kernel itself with the oracle."""
+them; the last test checks that the kernel source takes the same bounds.  The
+GPU parity tests compare the kernel itself with the oracle."""
+import os
+import re
+
 import numpy as np
 import pytest
 
 scipy_special = pytest.importorskip("scipy.special")
 
 SQPI = np.sqrt(np.pi)
+
+# The bounds each rule is held to below, and that the kernel must use.
+RING_MIN, RING_C = 26.0, 1.13e9      # R8(y) = min(64, max(26, ln(1.13e9) - ln y))
+K2, Z2 = 7, 3.0                       # two nodes: 7 terms when every |z| <= 3
+K3, Z3 = 12, 7.0                      # two nodes: 12 terms when every |z| <= 7
+K4, Y4, D4 = 12, 1.2, 0.2             # four nodes: y <= 1.2, |d| <= 0.2
+KW, KWF, WNEAR, WFAR, WZMAX = 12, 4, 5.0, 100.0, 1000.0   # wide lines
 
 
 def gh_pairs(n):
@@ -26,7 +37,7 @@ def gh_pairs(n):
 
 
 def ring_r2(y):
-    return np.minimum(64.0, np.maximum(26.0, np.log(1.13e9) - np.log(y)))
+    return np.minimum(64.0, np.maximum(RING_MIN, np.log(RING_C) - np.log(y)))
 
 
 def test_ring_rule_meets_its_bound():
@@ -109,8 +120,8 @@ def test_two_node_round_series():
         ok = np.ones(bins.size, bool)
         for b, cen, y, s in lines:
             ok &= ((bins - cen) * b) ** 2 + y * y >= 2500.0
-        got, zmax = series(bins[ok], lines, two_nodes(), 7)
-        if zmax > 3.0 or not ok.any():
+        got, zmax = series(bins[ok], lines, two_nodes(), K2)
+        if zmax > Z2 or not ok.any():
             continue
         used += 1
         ref = lorentz_direct(bins[ok], lines, two_nodes())
@@ -128,8 +139,8 @@ def test_two_node_round_series_twelve_terms():
         ok = np.ones(bins.size, bool)
         for b, cen, y, s in lines:
             ok &= ((bins - cen) * b) ** 2 + y * y >= 2500.0
-        got, zmax = series(bins[ok], lines, two_nodes(), 12)
-        if zmax > 7.0 or zmax <= 3.0 or not ok.any():
+        got, zmax = series(bins[ok], lines, two_nodes(), K3)
+        if zmax > Z3 or zmax <= Z2 or not ok.any():
             continue
         used += 1
         ref = lorentz_direct(bins[ok], lines, two_nodes())
@@ -144,14 +155,14 @@ def test_four_node_round_series():
     worst = 0.0
     for _ in range(300):
         b0 = rng.uniform(0.8, 3.0)
-        lines = [(b0 * (1 + rng.uniform(-2e-7, 2e-7)), rng.uniform(-0.2, 0.2) / b0,
-                  10 ** rng.uniform(-4, np.log10(1.2)), 10 ** rng.uniform(-3, 0))
+        lines = [(b0 * (1 + rng.uniform(-2e-7, 2e-7)), rng.uniform(-D4, D4) / b0,
+                  10 ** rng.uniform(-4, np.log10(Y4)), 10 ** rng.uniform(-3, 0))
                  for _ in range(32)]
         bins = np.arange(-300, 301, dtype=float)
         ok = np.ones(bins.size, bool)
         for b, cen, y, s in lines:
             ok &= ((bins - cen) * b) ** 2 + y * y >= 64.0
-        got, _ = series(bins[ok], lines, four_nodes(), 12)
+        got, _ = series(bins[ok], lines, four_nodes(), K4)
         ref = lorentz_direct(bins[ok], lines, four_nodes())
         worst = max(worst, np.max(np.abs(got - ref) / ref))
     assert worst <= 1e-7
@@ -161,7 +172,7 @@ def test_wide_round_series():
     """Wide lines: 12 terms where |x| >= 5 |z|max, 4 terms where |x| >= 100
     |z|max, centre offsets up to 300 bins, every line in its two-node band."""
     rng = np.random.default_rng(14)
-    worst = {12: 0.0, 4: 0.0}
+    worst = {KW: 0.0, KWF: 0.0}
     for _ in range(200):
         b0 = rng.uniform(0.1, 3.0)
         c0 = rng.uniform(0, 1)
@@ -169,10 +180,10 @@ def test_wide_round_series():
         lines = [(b0 * (1 + rng.uniform(-1e-3, 1e-3)) if j else b0,
                   c0 + (rng.uniform(-span, span) if j else 0.0),
                   10 ** rng.uniform(-6, 1.5), 10 ** rng.uniform(-3, 0)) for j in range(32)]
-        _, zmax = series(np.array([1e9]), lines, two_nodes(), 12)
-        if zmax > 1000.0:
+        _, zmax = series(np.array([1e9]), lines, two_nodes(), KW)
+        if zmax > WZMAX:
             continue
-        for lo, hi, K in [(5, 100, 12), (100, 3000, 4)]:
+        for lo, hi, K in [(WNEAR, WFAR, KW), (WFAR, 30 * WFAR, KWF)]:
             xs = np.concatenate([np.linspace(lo * zmax, hi * zmax, 200),
                                  -np.linspace(lo * zmax, hi * zmax, 200)])
             bins = c0 + xs / b0
@@ -181,7 +192,34 @@ def test_wide_round_series():
                 ok &= ((bins - cen) * b) ** 2 + y * y >= 2500.0
             if not ok.any():
                 continue
-            got, _ = series(bins[ok], lines, two_nodes(), 12, K)
+            got, _ = series(bins[ok], lines, two_nodes(), KW, K)
             ref = lorentz_direct(bins[ok], lines, two_nodes())
             worst[K] = max(worst[K], np.max(np.abs(got - ref) / ref))
-    assert worst[12] <= 1e-7 and worst[4] <= 1e-7, worst
+    assert worst[KW] <= 1e-7 and worst[KWF] <= 1e-7, worst
+
+
+def test_kernel_uses_the_tested_bounds():
+    """The FP32C kernel's series and ring constants are the ones the tests
+    above hold to their bounds (read from its source, so that a change to
+    either side without the other fails here)."""
+    src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2101_02005_gb300", "csrc",
+                            "hk_gather_f32.cu")).read()
+
+    def has(pattern):
+        assert re.search(pattern, src), pattern
+
+    def num(x):
+        return r"%s(?:\.0*)?f" % re.escape(repr(float(x)).rstrip("0").rstrip("."))
+
+    has(r"constexpr int KMP2 = %d, KMP4 = %d;" % (K2, K4))
+    assert K3 == K4   # the 12-term two-node form reuses KMP4
+    has(r"const bool ok4 = base & \(q\.y <= %s\) & \(fabsf\(d\) <= %s\);" % (num(Y4), num(D4)))
+    has(r"ok2 = base & \(zz <= %s\), ok3 = base & \(zz <= %s\);" % (num(Z2 ** 2), num(Z3 ** 2)))
+    has(r"mode == 3 \? KMP4 : KMP2")
+    has(r"constexpr int KW = %d, KWF = %d;" % (KW, KWF))
+    has(r"!\(zm <= %s\)" % num(WZMAX))
+    has(r"left_of\(%s \* zm\), gr = right_of\(%s \* zm\)" % (num(WNEAR), num(WNEAR)))
+    has(r"left_of\(%s \* zm\), gr4 = right_of\(%s \* zm\)" % (num(WFAR), num(WFAR)))
+    m = re.search(r"fmaxf\(([0-9.]+)f, ([0-9.]+)f - __logf\(y\)\)", src)
+    assert m and float(m.group(1)) == RING_MIN
+    assert abs(float(m.group(2)) - np.log(RING_C)) < 1e-6
