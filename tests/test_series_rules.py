@@ -1,14 +1,15 @@
-"""The accuracy claims of the FP32C kernel's batch rules, checked in FP64 on the
-CPU (no GPU): the 8-node Gauss-Hermite ring of the short-line core, and the
+"""The accuracy claims of the FP32C kernel's band rules, checked in FP64 on the
+CPU (no GPU): the float core's 18-node trapezoid with its pole term, the
+8-node Gauss-Hermite ring of the short-line core, and the
 series in 1/x that sums a warp's 32 lines at once (two-node form over the
 short-line interiors, four-node form over everything outside the r2 < 64
 union, the wide-line form with 12 and 4 terms).  Each rule is written here
 from its definition -- Gauss-Hermite nodes from numpy, the Lorentzian
 expansion 1/((x-a)^2 + c^2) = Im(1/(x - z))/c, 1/(x - z) = sum z^m / x^(m+1)
--- and compared with the direct sums (scipy's wofz for the ring), on seeded
-rounds built like the kernel's, with the bounds the kernel uses to choose
-them; the last test checks that the kernel source takes the same bounds.  The
-GPU parity tests compare the kernel itself with the oracle."""
+-- and compared with the direct sums (scipy's wofz for the core and the ring),
+on seeded rounds built like the kernel's, with the bounds the kernel uses to
+choose them; two tests check that the kernel source takes the same bounds.
+The GPU parity tests compare the kernel itself with the oracle."""
 import os
 import re
 
@@ -223,3 +224,55 @@ def test_kernel_uses_the_tested_bounds():
     m = re.search(r"fmaxf\(([0-9.]+)f, ([0-9.]+)f - __logf\(y\)\)", src)
     assert m and float(m.group(1)) == RING_MIN
     assert abs(float(m.group(2)) - np.log(RING_C)) < 1e-6
+
+
+# The float core rule: the trapezoid rule of step h = 1/2 with the pole
+# correction (Chiarella and Reichel 1968; Matta and Reichel 1971), on the
+# nodes n = -8 .. 9 of the lattice chosen so that no node lies within h/4 of x.
+CORE_N0, CORE_N1, CORE_H, CORE_YCORR = -8, 9, 0.5, 2.0
+
+
+def core_rule(x, y):
+    """Re w(x + iy) by the truncated trapezoid rule with its pole term, in
+    complex FP64: w(z) ~ (i h / pi) sum_n e^{-t_n^2} / (z - t_n)
+    + 2 e^{-z^2} / (1 -+ e^{-2 pi i z / h}) (minus on the lattice t_n = n h,
+    plus on t_n = (n + 1/2) h; the pole term only for y < 2)."""
+    z = x + 1j * y
+    fr = (x / CORE_H) % 1.0
+    shift = ~((fr > 0.25) & (fr < 0.75))
+    off = np.where(shift, 0.5, 0.0)
+    s = np.zeros(x.shape, complex)
+    for n in range(CORE_N0, CORE_N1 + 1):
+        t = (n + off) * CORE_H
+        s += np.exp(-t * t) / (z - t)
+    w = 1j * CORE_H / np.pi * s
+    e = np.exp(-2j * np.pi * z / CORE_H)
+    pole = 2.0 * np.exp(-z * z) / np.where(shift, 1.0 + e, 1.0 - e)
+    w = w + np.where(y < CORE_YCORR, pole, 0.0)
+    return w.real
+
+
+def test_core_rule_meets_its_bound():
+    """18 nodes over r2 < 64 (x >= 0, y from 1e-6 to 8): within 2e-8 of Re w."""
+    rng = np.random.default_rng(16)
+    r2 = rng.uniform(0, 64, 400000)
+    y = np.concatenate([10 ** rng.uniform(-6, np.log10(8), 200000), rng.uniform(0, 8, 200000)])
+    ok = y * y < r2
+    y, r2 = y[ok], r2[ok]
+    x = np.sqrt(r2 - y * y)
+    got = core_rule(x, y)
+    ref = scipy_special.wofz(x + 1j * y).real
+    assert np.max(np.abs(got - ref) / ref) <= 2e-8
+
+
+def test_core_rule_matches_the_kernel_source():
+    """The float core loop takes the nodes, step, lattice rule and pole-term
+    range that the test above holds to its bound."""
+    src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2101_02005_gb300", "csrc",
+                            "hk_internal.cuh")).read()
+    body = src[src.index("core_re(R x, R y)"):src.index("// Re w for any band")]
+    fl = body[body.index("if constexpr (sizeof(R) == 4)"):body.index("} else {")]
+    assert "for (int n = %d; n <= %d; ++n)" % (CORE_N0, CORE_N1) in fl
+    assert "R u = ax * R(%d);" % round(1 / CORE_H) in body
+    assert "bool sh = !(fr > R(0.25) && fr < R(0.75));" in body
+    assert "if (y < R(%d)) {" % CORE_YCORR in body
