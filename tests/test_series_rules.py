@@ -1,6 +1,7 @@
 """The accuracy claims of the FP32C kernel's band rules, checked in FP64 on the
-CPU (no GPU): the float core's 18-node trapezoid with its pole term, the
-8-node Gauss-Hermite ring of the short-line core, and the
+CPU (no GPU): the one- to four-node Gauss-Hermite bands, the float core's
+18-node trapezoid with its pole term, the 8-node Gauss-Hermite ring of the
+short-line core, and the
 series in 1/x that sums a warp's 32 lines at once (two-node form over the
 short-line interiors, four-node form over everything outside the r2 < 64
 union, the wide-line form with 12 and 4 terms).  Each rule is written here
@@ -8,7 +9,7 @@ from its definition -- Gauss-Hermite nodes from numpy, the Lorentzian
 expansion 1/((x-a)^2 + c^2) = Im(1/(x - z))/c, 1/(x - z) = sum z^m / x^(m+1)
 -- and compared with the direct sums (scipy's wofz for the core and the ring),
 on seeded rounds built like the kernel's, with the bounds the kernel uses to
-choose them; two tests check that the kernel source takes the same bounds.
+choose them; three tests check that the kernel source takes the same bounds.
 The GPU parity tests compare the kernel itself with the oracle."""
 import os
 import re
@@ -276,3 +277,38 @@ def test_core_rule_matches_the_kernel_source():
     assert "R u = ax * R(%d);" % round(1 / CORE_H) in body
     assert "bool sh = !(fr > R(0.25) && fr < R(0.75));" in body
     assert "if (y < R(%d)) {" % CORE_YCORR in body
+
+
+# The Gauss-Hermite bands by r2 = x^2 + y^2: (nodes, lower r2 bound, upper
+# r2 bound, the relative error each is held to).
+GH_BANDS = [(1, 1.5e6, 1e12, 1.0e-6), (2, 2500.0, 1.5e6, 4.1e-7), (3, 200.0, 2500.0, 7e-7),
+            (4, 64.0, 200.0, 1.0e-6)]
+
+
+def test_gauss_hermite_bands_meet_their_bounds():
+    """Each band's n-node Gauss-Hermite rule for w = (i/pi) int e^{-t^2}/(z - t) dt
+    (nodes and weights from numpy) is within its stated relative error of
+    scipy's Re w over the band, y from 1e-9 sqrt(r2) to sqrt(r2)."""
+    rng = np.random.default_rng(17)
+    for n, lo, hi, bound in GH_BANDS:
+        t, w = np.polynomial.hermite.hermgauss(n)
+        r2 = np.exp(rng.uniform(np.log(lo), np.log(hi), 200000))
+        f = np.concatenate([10 ** rng.uniform(-9, 0, 100000), rng.uniform(0, 1, 100000)])
+        y = np.sqrt(r2) * f
+        x = np.sqrt(np.maximum(r2 - y * y, 0.0))
+        z = x + 1j * y
+        got = (1j / np.pi * sum(wj / (z - tj) for tj, wj in zip(t, w))).real
+        ref = scipy_special.wofz(z).real
+        keep = ref > 0
+        err = np.max(np.abs(got[keep] - ref[keep]) / ref[keep])
+        assert err <= bound * (1 + 1e-3), (n, err)
+
+
+def test_band_limits_match_the_kernel_source():
+    src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2101_02005_gb300", "csrc",
+                            "hk_internal.cuh")).read()
+    m = re.search(r"core = R\(([0-9.e]+)\), gh4 = R\(([0-9.e]+)\), gh3 = R\(([0-9.e]+)\), "
+                  r"gh2 = R\(([0-9.e]+)\);", src)
+    assert m, "BandLimits"
+    core, gh4, gh3, gh2 = (float(v) for v in m.groups())
+    assert (gh2, gh3, gh4, core) == tuple(b[1] for b in GH_BANDS)
