@@ -23,6 +23,14 @@
 //   8-node Gauss-Hermite rule between it and r2 = 64).  The Lorentzian
 //   profile is the one-node band on every group; the Doppler and
 //   binned-Gaussian profiles run one formula per line in their own instances.
+// * Short lines go in batches of NLS co-located lines that share one sweep per
+//   group.  When all 32 lines of a round share their centre bin and groups,
+//   their two- or four-node values over the interior groups are one series in
+//   1/x about line 0 (coefficients taken lane-parallel and summed by
+//   shuffles): one reciprocal and a Horner sum per bin for the whole round.
+//   Wide Voigt lines take the same kind of series over the far groups of a
+//   tile where every line of the round is inside its cut and its two-node
+//   band, and batches of NLB lines on the rest.
 // * Each warp adds into its own FP32 copy of the tile in shared memory
 //   (consecutive bins, no bank conflicts, no atomics); every FLUSH_ROUNDS
 //   rounds the copies are summed into a (hi, lo) two-sum pair per bin, and at
