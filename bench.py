@@ -44,7 +44,7 @@ METRIC = "lines/s and Voigt evals/s on 1 GB300 (FP32-comp vs FP64 GPU) at stated
 # take out of the core count.
 FLOPS_PER_PAIR = {"gh1": 8, "gh2": 14, "gh3": 25, "gh4": 25, "ring8": 45, "core": 200}
 # DRAM bytes per line of one k_gather_f32 launch, from the ncu capture in
-# profiles/k_gather_f32_config1-5e7-lines.md (1201.8 MB read + 4.6 MB written for
+# profiles/k_gather_f32_config1-5e7-lines.md (1201.6 MB read + 4.9 MB written for
 # 5e7 lines; the line list is read once, so traffic grows with the line
 # count).  Set to None when the kernel changes.
 GATHER_DRAM_BYTES_PER_LINE = 24.13
