@@ -1,4 +1,5 @@
-"""The N > 1 host logic of bench.py on CPU: two processes over gloo.
+"""The host logic of bench.py on CPU: the N > 1 path with two processes over
+gloo, and the roofline arithmetic of the bench line.
 
 Multi-GPU runs of the benchmark are independent replicas (weak scaling, no
 data-path collective): the only cross-rank operations are the barrier and the
@@ -80,3 +81,31 @@ def test_reference_arm_rank0_only_under_torchrun():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_alu_roofline_arithmetic():
+    """The roofline object of the bench line: achieved = cost-model flops /
+    launch time, peak = 2 x the measured FMA rate, frac = their ratio, and the
+    nominal figure from the SM count x 128 lanes x 2 x the maximum clock."""
+    import bench
+
+    class Props:
+        multi_processor_count = 152
+
+    peaks = {"ffma": {"ops_per_s": 3.86e13, "sm_mhz": 2070.0, "reasons": []}}
+    r = bench.alu_roofline(4.26e12, 98.48, peaks, Props(), 2070.0)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(4.26e12 / 0.09848 / 1e12)
+    assert r["peak"] == pytest.approx(77.2)
+    assert r["frac"] == pytest.approx(r["achieved"] / 77.2)
+    assert r["peak_nominal"] == pytest.approx(152 * 128 * 2 * 2070e6 / 1e12)
+    assert "measured" in r["peak_basis"]
+
+
+def test_cost_model_covers_every_counted_band():
+    """Every band hk_count_pairs and hk_count_ring_pairs report has a cost, and
+    the cheaper rules never cost more than the ones they replace."""
+    import bench
+    c = bench.FLOPS_PER_PAIR
+    assert set(c) == {"gh1", "gh2", "gh3", "gh4", "ring8", "core"}
+    assert c["gh1"] < c["gh2"] < c["gh4"] <= c["ring8"] < c["core"]
