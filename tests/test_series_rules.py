@@ -292,8 +292,12 @@ def test_gauss_hermite_bands_meet_their_bounds():
     rng = np.random.default_rng(17)
     for n, lo, hi, bound in GH_BANDS:
         t, w = np.polynomial.hermite.hermgauss(n)
-        r2 = np.exp(rng.uniform(np.log(lo), np.log(hi), 200000))
+        # log-uniform over the band, plus dense points on its lower edge, where
+        # each rule's error peaks
+        r2 = np.concatenate([np.exp(rng.uniform(np.log(lo), np.log(hi), 180000)),
+                             np.full(20000, lo)])
         f = np.concatenate([10 ** rng.uniform(-9, 0, 100000), rng.uniform(0, 1, 100000)])
+        rng.shuffle(f)
         y = np.sqrt(r2) * f
         x = np.sqrt(np.maximum(r2 - y * y, 0.0))
         z = x + 1j * y
