@@ -104,3 +104,58 @@ def test_new_options_validated_on_host(hk):
     assert L.hk_set_tuning(hk.HK_FP64, 2048, 1024) == hk.HK_EINVAL    # FP64 tiles: 512
     v = ctypes.c_int(0)
     assert L.hk_tuning(7, b(v), None) == hk.HK_EINVAL
+
+
+def test_other_entry_points_validate_on_host(hk):
+    """The instrumentation, no-allocation, batched, adjoint and accumulate
+    entry points reject bad arguments before any device work."""
+    L = hk.lib()
+    b = ctypes.byref
+    lines = hk.hk_lines(1, 2, None, None, 3, 4, 5, 10, 18.0, 0, 1)
+    unsorted = hk.hk_lines(1, 2, None, None, 3, 4, 5, 10, 18.0, 0, 0)
+    grid = hk.make_grid(0.0, 0.1, 100)
+    st = hk.make_state(1000.0, 1.0, 3000.0)
+    op = hk.make_opts(500.0, 25.0)
+    assert L.hk_count_pairs(b(lines), b(grid), b(st), b(op), None, None) == hk.HK_EINVAL
+    assert L.hk_count_ring_pairs(b(lines), b(grid), b(st), b(op), None, None) == hk.HK_EINVAL
+    ms, n = ctypes.c_double(0), ctypes.c_int64(0)
+    assert L.hk_profile(2, b(ms), b(n)) == hk.HK_EINVAL
+    v = ctypes.c_double(0)
+    for kind, target, out in ((5, 100.0, b(v)), (-1, 100.0, b(v)), (0, 0.0, b(v)),
+                              (0, 1e5, b(v)), (0, float("nan"), b(v)), (0, 100.0, None)):
+        assert L.hk_measure_peak(kind, target, out, None) == hk.HK_EINVAL
+    # no-allocation entry: an output is required and the list must be sorted
+    assert L.hk_cross_section_noalloc(b(lines), b(grid), b(st), b(op), None, None) == hk.HK_EINVAL
+    assert L.hk_cross_section_noalloc(b(unsorted), b(grid), b(st), b(op), 1, None) == \
+        hk.HK_ENOTSUP
+    # batched: counts, outputs and precision
+    two = (hk.hk_lines * 2)(lines, lines)
+    sts = (hk.hk_state * 2)(st, st)
+    for ns, nt in ((0, 2), (2, 0), (-1, 2)):
+        assert L.hk_cross_section_batched(two, ns, sts, nt, b(grid), b(op), 1, 1, 1 << 30,
+                                          None) == hk.HK_EINVAL
+    assert L.hk_cross_section_batched(two, 2, sts, 2, b(grid), b(op), None, 1, 1 << 30,
+                                      None) == hk.HK_EINVAL
+    op64 = hk.make_opts(500.0, 25.0, precision=hk.HK_FP64)
+    assert L.hk_cross_section_batched(two, 2, sts, 2, b(grid), b(op64), 1, 1, 1 << 30,
+                                      None) == hk.HK_ENOTSUP
+    # adjoint: points, upstream gradient and outputs; options it does not cover
+    assert L.hk_cross_section_backward(b(lines), b(grid), sts, 0, b(op), 1, 1, 1, 1, 1, 1,
+                                       1 << 30, None) == hk.HK_EINVAL
+    assert L.hk_cross_section_backward(b(lines), b(grid), sts, 2, b(op), None, 1, 1, 1, 1, 1,
+                                       1 << 30, None) == hk.HK_EINVAL
+    assert L.hk_cross_section_backward(b(lines), b(grid), sts, 2, b(op), 1, 1, 1, None, 1, 1,
+                                       1 << 30, None) == hk.HK_EINVAL
+    opp = hk.make_opts(500.0, 25.0, flags=hk.HK_REMOVE_PLINTH)
+    assert L.hk_cross_section_backward(b(lines), b(grid), sts, 2, b(opp), 1, 1, 1, 1, 1, 1,
+                                       1 << 30, None) == hk.HK_ENOTSUP
+    # the bare accumulate: line count, precision, cut and pointers
+    assert L.hk_voigt_accumulate(1, 2, 3, 4, -1, b(grid), 25.0, 5, hk.HK_FP32C, None) == \
+        hk.HK_EINVAL
+    assert L.hk_voigt_accumulate(1, 2, 3, 4, 10, b(grid), 25.0, 5, 7, None) == hk.HK_EINVAL
+    assert L.hk_voigt_accumulate(1, 2, 3, 4, 10, b(grid), float("inf"), 5, hk.HK_FP32C,
+                                 None) == hk.HK_EINVAL
+    assert L.hk_voigt_accumulate(None, 2, 3, 4, 10, b(grid), 25.0, 5, hk.HK_FP32C, None) == \
+        hk.HK_EINVAL
+    assert L.hk_voigt_accumulate(1, 2, 3, 4, 10, b(grid), 25.0, None, hk.HK_FP32C, None) == \
+        hk.HK_EINVAL
