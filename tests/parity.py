@@ -166,3 +166,31 @@ def sampled_errors(gpu_full, L, grid, state, cut, seed):
                 max_bin=float(np.max(d[m] / ref[m])) if m.any() else 0.0,
                 l1=float(d[m].sum() / ref[m].sum()) if m.any() else 0.0,
                 below_mask_abs=float(d[~m].max()) if (~m).any() else 0.0, ref_max=ref_max)
+
+
+# Lorentz widths gamma_ref (cm^-1) of the four cluster kinds of the round-series
+# case, at 1500 K and 1 bar: y near 0.4 (the four-node series), 1.8 (two nodes,
+# 7 terms), 5 (two nodes, 12 terms) and 21 (no series).
+ROUND_SERIES_GAMMA = (0.05, 0.25, 0.7, 3.0)
+
+
+def round_series_case(seed):
+    """Short lines in 16 clusters of 128 lines within 0.02 bins of a bin centre
+    (0.1 cm^-1 bins from 14000 cm^-1, 9000 bins), the clusters cycling through
+    ROUND_SERIES_GAMMA, so that whole 32-line rounds share their centre bin;
+    modest strengths and lower-state energies.  Returns (lines, grid)."""
+    from paper_2101_02005_gb300 import synth
+    rng = np.random.default_rng(seed)
+    dnu, nu_min, nbins = 0.1, 14000.0, 9000
+    nu0, gam = [], []
+    for i, k in enumerate(np.linspace(400, nbins - 400, 16).astype(int)):
+        base = nu_min + k * dnu
+        nu0.extend((base + np.sort(rng.uniform(-2e-3, 2e-3, 128))).tolist())
+        g = ROUND_SERIES_GAMMA[i % 4]
+        gam.extend((g * rng.uniform(0.85, 1.0, 128)).tolist())
+    nu0 = np.asarray(nu0)
+    n = nu0.size
+    L = synth.LineList(nu0, (10 ** rng.uniform(-22, -20, n)).astype(np.float32),
+                       rng.exponential(300.0, n).astype(np.float32),
+                       np.asarray(gam, np.float32), np.full(n, 0.5, np.float32), 18.0)
+    return L, synth.Grid(nu_min, dnu, nbins)

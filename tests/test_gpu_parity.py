@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 from parity import (assert_plinth_close, assert_sigma_close, oracle_sigma_max, record,
-                    sigma_errors)
+                    round_series_case, sigma_errors)
 from paper_2101_02005_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -791,21 +791,10 @@ def test_round_series_parity(hk, plinth):
     0.4 (four nodes), 1.8 (two nodes, 7 terms), 5 (two nodes, 12 terms) and 21
     (no series), at nu0 ~ 14500 cm^-1 (x step ~1.7 per bin, as at config 1);
     modest strengths and lower-state energies keep the whole array above the
-    mask, so every bin is held to the bar.  FP32C against the oracle."""
-    rng = np.random.default_rng(31 + plinth)
-    dnu, nu_min, nbins = 0.1, 14000.0, 9000
-    nu0, gam = [], []
-    for i, k in enumerate(np.linspace(400, nbins - 400, 16).astype(int)):
-        base = nu_min + k * dnu
-        nu0.extend((base + np.sort(rng.uniform(-2e-3, 2e-3, 128))).tolist())
-        g = [0.05, 0.25, 0.7, 3.0][i % 4]
-        gam.extend((g * rng.uniform(0.85, 1.0, 128)).tolist())
-    nu0 = np.asarray(nu0)
-    n = nu0.size
-    L = synth.LineList(nu0, (10 ** rng.uniform(-22, -20, n)).astype(np.float32),
-                       rng.exponential(300.0, n).astype(np.float32),
-                       np.asarray(gam, np.float32), np.full(n, 0.5, np.float32), 18.0)
-    grid = synth.Grid(nu_min, dnu, nbins)
+    mask, so every bin is held to the bar.  FP32C against the oracle
+    (tests/test_series_rules.py checks on the CPU that each cluster kind meets
+    its form's conditions)."""
+    L, grid = round_series_case(31 + plinth)
     T, P = 1500.0, 1.0
     flags = hk.HK_SIGMA_F64 | (hk.HK_REMOVE_PLINTH if plinth else 0)
     got = gpu_sigma(hk, L, grid, T, P, 25.0, 0, flags=flags)

@@ -316,3 +316,41 @@ def test_band_limits_match_the_kernel_source():
     assert m, "BandLimits"
     core, gh4, gh3, gh2 = (float(v) for v in m.groups())
     assert (gh2, gh3, gh4, core) == tuple(b[1] for b in GH_BANDS)
+
+
+def test_round_series_case_takes_each_form():
+    """The GPU parity case for the round series (tests/parity.py) builds, in
+    each cluster kind, 32-line rounds that meet exactly one form's conditions
+    as the kernel decides them: a shared centre bin, then four nodes (every
+    y <= 1.2 and |d| <= 0.2), else two nodes with 7 terms (every |z| <= 3),
+    else 12 terms (every |z| <= 7), else no series."""
+    import oracle
+    from parity import ROUND_SERIES_GAMMA, round_series_case
+    L, grid = round_series_case(31)
+    nu_min, dnu, _ = grid.astuple()
+    aD, GL = oracle.widths(L.nu0, L.gamma_ref, L.n_T, 1500.0, 1.0, L.mass_amu)
+    y_all = GL / aD
+    b_all = dnu / aD                           # x step per bin
+    u = (L.nu0 - nu_min) / dnu
+    c_all = np.rint(u)
+    rn_all = u - c_all                         # centre offset from the nearest bin
+    t = 1.0 / np.sqrt(2.0)
+    forms = []
+    for r in range(L.n // 32):
+        s = slice(32 * r, 32 * r + 32)
+        c, y, b, rn = c_all[s], y_all[s], b_all[s], rn_all[s]
+        assert np.all(c == c[0])
+        d = (rn[0] - rn) * b
+        beta = b / b[0]
+        zz = np.maximum(((t - d) / beta) ** 2, ((-t - d) / beta) ** 2) + (y / beta) ** 2
+        if np.all(y <= Y4) and np.all(np.abs(d) <= D4):
+            forms.append(4)
+        elif np.all(zz <= Z2 * Z2):
+            forms.append(2)
+        elif np.all(zz <= Z3 * Z3):
+            forms.append(3)
+        else:
+            forms.append(0)
+    # clusters of 4 rounds cycle through the widths: four nodes, 7 terms, 12 terms, none
+    assert len(ROUND_SERIES_GAMMA) == 4
+    assert forms == ([4] * 4 + [2] * 4 + [3] * 4 + [0] * 4) * 4
